@@ -1,0 +1,62 @@
+"""Workload presets: procedural box-room scenes sized like the paper's workloads.
+
+The paper's own scenes (Bedroom, Tearoom, Museum; Table 1) are not available, so
+seeded procedural scenes stand in for them.  Each preset fixes the scene recipe
+(image size, VPL count, occluder boxes, materials) and the method's parameters
+(slice count, sampling rate, rank, iteration count, cut bound).  Parameters are
+plain numbers: no arithmetic of the method lives here.
+"""
+from __future__ import annotations
+
+import copy
+
+# Common method parameters (readings of the paper; Sec. 3-5):
+#   eps_cut   lightcuts relative error bound for the conservative global cut (Sec. 3 item 1)
+#   max_cut   cap on the global cut size (the paper's cuts hold ~800-900 nodes)
+#   tau       coarsening threshold relative to the slice's estimated mean pixel (Eq. 2)
+#   rate      sampling rate rho = |Omega_s| / (m'_s n'_s)  (Sec. 5)
+#   rank      completion rank r (the paper's q, Sec. 5)
+#   als_iters fixed number of alternating least-squares sweeps
+#   lam_rel   ridge term relative to the mean Gram diagonal
+_BASE = dict(
+    light_power=1.0,
+    light_size=0.2,
+    eps_cut=0.05,
+    tau=0.02,
+    lam_rel=1e-4,
+    d_min=0.01,
+    slice_feature_normal_weight=0.3,
+    kmeans_iters=10,
+    frame_seed=7,
+)
+
+CONFIGS = {
+    # 64x64 points, 1024 VPLs, two floor boxes: the oracle renders it in seconds.
+    "room64_vpl1k_2box": dict(
+        _BASE, width=64, height=64, n_vpl=1024, n_big_boxes=2, n_small_boxes=0,
+        glossy_frac=0.0, n_slices=16, rate=0.10, rank=8, als_iters=10,
+        max_cut=1024, scene_seed=1001,
+    ),
+    # 256x256 points, 16384 VPLs, 200 random boxes behind a uniform grid.
+    "room256_vpl16k_200box": dict(
+        _BASE, width=256, height=256, n_vpl=16384, n_big_boxes=0, n_small_boxes=200,
+        glossy_frac=0.0, n_slices=64, rate=0.05, rank=16, als_iters=10,
+        max_cut=4096, scene_seed=1002,
+    ),
+    # 512x512 points, 65536 VPLs, 1000 boxes, Phong lobe on 30% of faces.
+    "room512_vpl64k_1000box_glossy": dict(
+        _BASE, width=512, height=512, n_vpl=65536, n_big_boxes=0, n_small_boxes=1000,
+        glossy_frac=0.3, n_slices=128, rate=0.05, rank=16, als_iters=10,
+        max_cut=2000, scene_seed=1003,
+    ),
+}
+
+
+def get_config(name: str, **overrides) -> dict:
+    """Return a copy of preset ``name`` with ``overrides`` applied."""
+    if name not in CONFIGS:
+        raise KeyError(f"unknown workload {name!r}; known: {sorted(CONFIGS)}")
+    cfg = copy.deepcopy(CONFIGS[name])
+    cfg.update(overrides)
+    cfg["name"] = name
+    return cfg

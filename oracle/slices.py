@@ -1,0 +1,63 @@
+"""Matrix slicing: cluster the shading points by position and normal (Sec. 3 step 2).
+
+The paper partitions the rows of A by clustering the 6-D (coordinate, normal)
+vectors of the surface points, following the lightslice method (and implements it
+as a recursive binary split on the GPU, Sec. 6).  The reading taken here is Lloyd's
+k-means into S slices:
+
+* feature of point i: (p_x, p_y, p_z, w n_x, w n_y, w n_z), w = 0.3;
+* initial centroids: the points of rank floor((k + 1/2) m / S), k = 0..S-1, in the
+  Morton order of the positions (codes as in the light tree, normalised to the
+  points' bounding box; ties by pixel index);
+* ``iters`` rounds of (assign every point to the nearest centroid in squared
+  Euclidean distance, ties to the lowest index; move every non-empty centroid to
+  the mean of its points); then a final assignment;
+* rows are made slice-contiguous: row_perm lists pixel indices sorted by (slice,
+  pixel index) and slice_off[s] .. slice_off[s+1] is slice s.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .tree import morton_codes
+
+
+def features(points, w=0.3) -> np.ndarray:
+    P = np.asarray(points, dtype=np.float64)
+    return np.concatenate([P[0, :, :3], w * P[1, :, :3]], axis=1)
+
+
+def assign(X: np.ndarray, C: np.ndarray, chunk: int = 8192) -> np.ndarray:
+    out = np.empty(X.shape[0], dtype=np.int64)
+    for s in range(0, X.shape[0], chunk):
+        d2 = np.sum((X[s:s + chunk, None, :] - C[None, :, :]) ** 2, axis=-1)
+        out[s:s + chunk] = np.argmin(d2, axis=1)
+    return out
+
+
+def kmeans_slices(points, n_slices: int, iters: int = 10, w: float = 0.3):
+    """Return (row_perm [m], slice_off [S+1], labels [m], centroids [S, 6])."""
+    X = features(points, w)
+    m = X.shape[0]
+    S = int(n_slices)
+    codes = morton_codes(np.asarray(points, dtype=np.float32)[0, :, :3])
+    keys = (codes << np.uint64(32)) | np.arange(m, dtype=np.uint64)
+    order = np.argsort(keys, kind="stable")
+    init = order[(2 * np.arange(S) + 1) * m // (2 * S)]
+    C = X[init].copy()
+    for _ in range(iters):
+        lab = assign(X, C)
+        for k in range(S):
+            sel = lab == k
+            if np.any(sel):
+                C[k] = X[sel].mean(axis=0)
+    lab = assign(X, C)
+    row_perm = np.argsort(lab, kind="stable")
+    counts = np.bincount(lab, minlength=S)
+    slice_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return row_perm.astype(np.int64), slice_off, lab, C
+
+
+def permute_points(points, row_perm) -> np.ndarray:
+    """Shading points in slice order."""
+    return np.ascontiguousarray(np.asarray(points)[:, row_perm, :])
