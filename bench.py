@@ -1,0 +1,326 @@
+"""Benchmark: ms per frame of the sparse sampling + completion renderer on one GB300.
+
+A step is one frame of the method's hot path (pass 1 + coarsening, pass 2, entry
+evaluation, masked-ALS completion of every slice, factorised render) on the
+256x256-point, 16384-VPL, 200-box room scene with 64 slices, 5% sampling, rank 16.
+Setup (light tree, global cut, slices) is timed separately and reported.  Quality
+is the rel-RMSE of the frame against the brute-force column sum over all VPLs
+(computed on the GPU by the library's brute-force kernel, which the tests check
+against the CPU oracle).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank renders its own frames of the same workload
+(independent problems, no collective on the data path; weak scaling).
+--impl reference times the CPU oracle (the plain float64 restatement of the method)
+on the host cores on a bounded sample of the same frame.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "room256_vpl16k_200box"
+METRIC = "ms/frame at rel-RMSE<=2% vs full-matrix render; speedup vs plain GPU form"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-slices", type=int, default=2, help="slices of the frame in the CPU sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(workload: str, n_slices_sample: int) -> dict:
+    """Time the CPU oracle on a bounded sample of one frame, in a fresh process with
+    single-threaded numpy, and scale to a whole frame by the rows processed."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+from ltinputs import get_config, make_scene
+from oracle import pipeline
+cfg = get_config({workload!r})
+sc = make_scene(cfg)
+st = pipeline.setup(sc, cfg)
+off = st["slice_off"]
+S = len(off) - 1
+pick = list(range(0, S, max(1, S // {n_slices_sample})))[:{n_slices_sample}]
+rows = int(sum(off[s + 1] - off[s] for s in pick))
+t0 = time.perf_counter()
+for s in pick:
+    pipeline.run_slice(st, sc, cfg, s, cfg["frame_seed"])
+dt = time.perf_counter() - t0
+print(json.dumps(dict(seconds=dt, rows=rows, m=int(sc.m), slices=pick)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    ms_frame = r["seconds"] * 1e3 * r["m"] / r["rows"]
+    return dict(value=ms_frame, unit="ms/frame", cores=1, kind="oracle",
+                sample=f"slices {r['slices']} ({r['rows']} of {r['m']} rows) of one frame, "
+                       f"{r['seconds']:.1f} s of CPU time, scaled by rows")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        pass  # the oracle has nothing to warm up; warm-up steps are not repeated on the CPU
+    for _ in range(max(1, args.steps)):
+        vals.append(oracle_sample(args.workload, args.cpu_slices))
+        if sum(v["value"] for v in vals) > 0 and len(vals) >= 1 and args.steps > 1:
+            # one bounded sample per step would take minutes; one sample stands for all steps
+            break
+    v = vals[0]
+    line = dict(impl="reference", metric=METRIC, value=round(v["value"], 3), unit="ms/frame",
+                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup, ms_per_step=round(v["value"], 3),
+                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload), cpu_baseline=v,
+                e2e=dict(value=round(v["value"], 3), unit="ms/frame", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ------------------------------------------------------------------ roofline
+# Algorithmic FP32 operations of one evaluated entry (counted from the source of
+# the entry model and the traversal): shading of the unoccluded value 40, ray set-up
+# and grid clipping 40 per shadow ray, 6 per grid cell visited, 24 per box slab test.
+OPS_ENTRY, OPS_RAY, OPS_CELL, OPS_BOX = 40, 40, 6, 24
+SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+
+
+def eval_roofline(lt, ctx, R, stage_ms, clk):
+    """ALU roofline of the entry-evaluation kernel (the shadow-ray kernel)."""
+    st = lt.lt_eval_stats(ctx, R.frame, R.smp, R.cfg["d_min"])
+    ops = OPS_ENTRY * st["entries"] + OPS_RAY * st["rays"] + OPS_CELL * st["cells"] + OPS_BOX * st["boxes"]
+    secs = stage_ms[2] * 1e-3
+    achieved = ops / secs / 1e12 if secs > 0 else 0.0
+    peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    return dict(bound="alu", kernel="k_eval_entries", achieved=round(achieved, 3), peak=round(peak, 2),
+                unit="TFLOP/s", frac=round(achieved / peak, 4), traffic=None,
+                peak_source="152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max SM clock",
+                work=dict(entries=st["entries"], rays=st["rays"], cells=st["cells"], boxes=st["boxes"],
+                          ops_per_launch=int(ops)))
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from ltinputs import get_config, make_scene
+    from paper_2202_12567_gb300 import lt
+    from paper_2202_12567_gb300.renderer import Renderer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+
+    cfg = get_config(args.workload)
+    sc = make_scene(cfg)
+    ctx = lt.Context(local)
+    R = Renderer(sc, cfg, device=local, ctx=ctx)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    R.setup()
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    seed0 = cfg["frame_seed"]
+
+    def frame(i, stage_events=None):
+        seed = seed0 + i
+        ev = stage_events
+        if ev:
+            ev[0].record()
+        R.pass1(seed)
+        if ev:
+            ev[1].record()
+        R.pass2(seed)
+        if ev:
+            ev[2].record()
+        R.evaluate()
+        if ev:
+            ev[3].record()
+        R.complete(seed)
+        if ev:
+            ev[4].record()
+        R.render_image()
+        if ev:
+            ev[5].record()
+
+    for i in range(args.warmup):
+        frame(i)
+    lt.lt_sync(ctx)
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lt.lt_launch_count(ctx)
+    clocks = ClockSampler(local)
+    per = []
+    stage_ms = np.zeros(5)
+    for k in range(args.steps):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        frame(1000 + k, evs)
+        torch.cuda.synchronize()
+        per.append(evs[0].elapsed_time(evs[5]))
+        stage_ms += np.array([evs[j].elapsed_time(evs[j + 1]) for j in range(5)])
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = lt.lt_launch_count(ctx) - launches0
+    lt.lt_sync(ctx)
+    total_ms = float(sum(per))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    stage_ms /= args.steps
+    ms_frame = total_ms / (args.steps * world)
+
+    # quality: the last frame against the brute-force column sum over all VPLs
+    img = R.img.clone()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    bf = torch.empty_like(img)
+    R.bruteforce(bf)  # warm
+    flush.zero_()
+    e0.record()
+    R.bruteforce(bf)
+    e1.record()
+    torch.cuda.synchronize()
+    bf_ms = e0.elapsed_time(e1)
+    rel = float(torch.linalg.norm(img.double() - bf.double()) / torch.linalg.norm(bf.double()))
+    rays_per_px = float(R.rays()) / R.frame.m
+
+    # end to end through the C ABI from pinned host buffers: points and VPLs in, image out
+    pts_h = torch.from_numpy(sc.points).pin_memory()
+    vpl_h = torch.from_numpy(sc.vpls).pin_memory()
+    img_h = torch.empty(R.frame.m, dtype=torch.float32).pin_memory()
+    e2e = []
+    for k in range(max(3, args.steps // 2) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.pts.copy_(pts_h, non_blocking=True)
+        R.vpls.copy_(vpl_h, non_blocking=True)
+        R.pts_s.copy_(lt.lt_permute_points(ctx, R.pts, R.row_perm))
+        frame(5000 + k)
+        img_h.copy_(R.img, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e.append(a.elapsed_time(b))
+    e2e_ms = statistics.mean(e2e)
+    h2d = sc.points.nbytes + sc.vpls.nbytes
+    d2h = img_h.numel() * 4
+
+    roof = eval_roofline(lt, ctx, R, stage_ms, clk)
+
+    line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                config=dict(workload=f"{args.workload}: 256x256 points, 16384 VPLs, 200 boxes, 64 slices, "
+                                     f"5% sampling, rank 16, 10 ALS sweeps",
+                            l2="flushed (256 MB write) between timed frames", global_cut=int(R.frame.C),
+                            rel_rmse_vs_bruteforce=round(rel, 5), rays_per_pixel=round(rays_per_px, 2),
+                            bruteforce_gpu_ms=round(bf_ms, 3), speedup_vs_bruteforce=round(bf_ms / ms_frame, 2),
+                            setup_ms=round(setup_ms, 1),
+                            stage_ms=dict(zip(["pass1", "pass2", "eval", "complete", "render"],
+                                              [round(x, 4) for x in stage_ms.tolist()]))),
+                e2e=dict(value=round(e2e_ms, 4), unit="ms/frame", h2d_bytes_per_step=int(h2d),
+                         d2h_bytes_per_step=int(d2h)),
+                gpu_launches=int(launches), clocks=clk, roofline=roof)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = oracle_sample(args.workload, args.cpu_slices)
+        except Exception as e:  # report, do not hide
+            line["cpu_baseline"] = dict(value=None, unit="ms/frame", cores=1, kind="oracle", sample=f"failed: {e}")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * lt.h - C ABI of the sparse lighting-matrix renderer (GB300 / sm_103a).
+ *
+ * Huo, Wang, Liu, Bao, "Sparse Sampling and Completion for Light Transport in
+ * VPL-based Rendering".  The lighting matrix A has one row per shading point and
+ * one column per VPL (or light-tree node); the image is the sum of its columns
+ * (Sec. 3).  The library never forms A: it samples entries per slice in two passes
+ * (Sec. 4 and 5), completes each slice at rank r and renders the image from the
+ * factors (Sec. 3, step 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an lt_status.  Argument errors are reported at once.
+ *   Kernels run asynchronously on the context's stream; a device-side error (a
+ *   loop bound or a capacity hit inside a kernel) is latched in a device status
+ *   word and returned by the next lt_sync().
+ * - Every array argument is a DEVICE pointer owned by the caller (typically a
+ *   PyTorch tensor) unless the name ends in _host.  The library never frees caller
+ *   memory.  The context owns only its scratch memory, grown on demand and released
+ *   by lt_destroy().  Base pointers of float4 planes must be 16-byte aligned.
+ * - Sizes are int64_t or int32_t as declared; seeds are uint64_t.
+ * - Shading points: float[3][m][4] planes  [px py pz albedo] [nx ny nz gloss]
+ *   [ox oy oz 0]   (o = unit direction to the camera, gloss 0 = diffuse).
+ * - VPLs: float[3][n][4] planes [px py pz albedo] [nx ny nz gloss] [ix iy iz flux]
+ *   (i = unit direction back towards the light the VPL was deposited from).
+ * - Occluders: float[nb][6] axis-aligned boxes [xmin ymin zmin xmax ymax zmax].
+ *
+ * Entry model (Sec. 3 problem statement; the paper gives no shading formula, the
+ * reading is): A(i,j) = flux_j f_i(w -> w_o) f_j(w_in -> -w) G V with
+ * G = max(0, n_i.w) max(0, -n_j.w) / max(d^2, d_min^2), f = albedo/pi or the
+ * normalised modified Phong mix, and V the shadow-ray test of the segment between
+ * the points offset by 1e-4 along their normals, restricted to t in
+ * (1e-4, 1 - 1e-4), against the closed occluder boxes.  A light-tree node c acts as
+ * its representative VPL scaled by I_c / I_rep(c) (Sec. 4), I = flux * albedo.
+ */
+#ifndef LT_H_
+#define LT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t lt_status;
+#define LT_OK 0
+#define LT_EINVAL 1      /* bad argument (null pointer, size out of range, misalignment) */
+#define LT_ENOMEM 2      /* scratch allocation failed */
+#define LT_ECUDA 3       /* a CUDA runtime call failed; lt_last_error() has the text */
+#define LT_ELIMIT 4      /* a device loop bound or a caller capacity was reached */
+#define LT_ENUMERIC 5    /* a non-finite value where a finite one was required */
+
+typedef struct lt_ctx lt_ctx;
+
+/* Light tree over n VPLs: 2n-1 nodes, internal nodes 0..n-2 (root 0), leaf j is
+ * node n-1+j and holds VPL order[j].  All arrays device, caller-allocated. */
+typedef struct {
+    int64_t n;
+    int32_t* order;    /* [n] VPL of leaf j (Morton order with the orientation class above) */
+    int32_t* child;    /* [2n-1][2] children, -1 on leaves */
+    int32_t* parent;   /* [2n-1] parent, -1 at the root */
+    int32_t* range;    /* [2n-1][2] first and last leaf index covered */
+    int32_t* rep;      /* [2n-1] representative VPL (child with the larger I, ties left) */
+    float* I;          /* [2n-1] intensity, I_f = I_a + I_b in float32 (Sec. 4) */
+    float* B;          /* [2n-1] max over the node's VPLs of f_max / albedo */
+    float* aabb;       /* [2n-1][6] lo xyz, hi xyz */
+} lt_tree;
+
+/* One frame's fixed inputs: slice-ordered points, VPLs, slices, tree and the
+ * global cut seen as a forest (the tree truncated at the cut). */
+typedef struct {
+    const float* pts;          /* [3][m][4] shading points in slice order */
+    int64_t m;
+    const float* vpls;         /* [3][n][4] */
+    int64_t n;
+    const int32_t* slice_off;  /* [S+1] rows of slice s: slice_off[s] .. slice_off[s+1]-1 */
+    int32_t S;
+    int32_t max_rows;          /* largest slice (host value, <= 65535) */
+    lt_tree tree;
+    int32_t C;                 /* global cut size (forest leaves) */
+    const int32_t* forest;     /* [2C-1][8] per forest node: tree node, child0, child1, parent,
+                                  first leaf, last leaf, height, 0.  Leaves 0..C-1 are the cut
+                                  in leaf order; internal nodes C..2C-2 its ancestors by tree id */
+    const int32_t* level_off;  /* [H+2] internal forest nodes of height h: level_nodes[level_off[h]..] */
+    const int32_t* level_nodes;/* [C-1] */
+    int32_t H;                 /* forest height (host value) */
+} lt_frame;
+
+/* Per-slice sampled entries Omega_s (Sec. 4-5).  Entry keys pack (row << 16) | col
+ * with row local to the slice and col an index into the slice's coarsened cut. */
+typedef struct {
+    int32_t* ncol;        /* [S] n'_s, columns of the coarsened cut */
+    int32_t* col_node;    /* [S][C] tree node of each column, leaf order */
+    float* g;             /* [S][C] column importance g = max - min of observed values (Sec. 5) */
+    const int64_t* off;   /* [S+1] capacity layout: slice s owns key/val[off[s] .. off[s+1]) */
+    uint32_t* key;        /* [off[S]] */
+    float* val;           /* [off[S]] */
+    int32_t* n1;          /* [S] pass-1 entries (first n1[s] of the slice) */
+    int32_t* cnt;         /* [S] all entries (pass 1 then pass 2) */
+} lt_samples;
+
+/* Completed factors: M_s ~= U_s V_s^T at rank r (the paper's X = U, Y = V^T). */
+typedef struct {
+    int32_t r;            /* rank, 1..32 */
+    float* U;             /* [m][r] rows in slice order */
+    float* V;             /* [S][C][r] */
+} lt_factors;
+
+const char* lt_status_str(lt_status s);
+const char* lt_last_error(const lt_ctx* ctx);
+
+/* Create a context on CUDA device `device`; every call of the context runs on
+ * `stream`, a cudaStream_t owned by the caller (NULL = the CUDA default stream). */
+lt_status lt_create(lt_ctx** ctx, int device, void* stream);
+lt_status lt_destroy(lt_ctx* ctx);
+/* Wait for the context's stream; return and clear the latched device status. */
+lt_status lt_sync(lt_ctx* ctx);
+/* Device status word (int32) that kernels latch errors into, for callers that
+ * poll it themselves. */
+int32_t* lt_status_word(lt_ctx* ctx);
+/* Number of kernels this context has launched so far (instrumentation). */
+int64_t lt_launch_count(const lt_ctx* ctx);
+/* Device address and size of scratch slot `slot` of the context (debugging aid:
+ * the layout of a slot is internal and may change). */
+lt_status lt_debug_scratch(lt_ctx* ctx, int32_t slot, void** ptr, int64_t* bytes);
+
+/* Occluders for the shadow rays (Sec. 6 casts rays against the scene; here a
+ * uniform grid over the boxes, res^3 cells, res 0 = automatic).  The grid is built
+ * on the host from a copy of the boxes and kept in the context.  nb may be 0. */
+lt_status lt_scene_upload(lt_ctx* ctx, const float* boxes, int64_t nb, int32_t grid_res);
+
+/* Shadow test of k segments org[k][3] -> end[k][3] over t in (1e-4, 1 - 1e-4):
+ * blocked[k] = 1 if a closed box meets it (no offsets applied). */
+lt_status lt_shadow_test(lt_ctx* ctx, const float* org, const float* end, int64_t k,
+                         uint8_t* blocked);
+
+/* A(i, j) for `count` (point, VPL) pairs with the node factor scale[k]
+ * (NULL = 1): out[k] = scale[k] * A(rows[k], vpl[k]).  Sec. 3 entry definition. */
+lt_status lt_eval_pairs(lt_ctx* ctx, const float* pts, int64_t m, const float* vpls, int64_t n,
+                        const int32_t* rows, const int32_t* vpl, const float* scale,
+                        int64_t count, float d_min, float* out);
+
+/* Brute force: img[i] = sum_j A(i, j) over all n VPLs (the column sum of the full
+ * lighting matrix, Sec. 3; the reference images of the experiments). */
+lt_status lt_bruteforce(lt_ctx* ctx, const float* pts, int64_t m, const float* vpls, int64_t n,
+                        float d_min, float* img);
+
+/* ---- Step 1 (Sec. 3): light tree and conservative global light cut ---------- */
+/* Build the light tree of the VPLs into caller arrays sized for n. */
+lt_status lt_build_tree(lt_ctx* ctx, const float* vpls, int64_t n, lt_tree* tree);
+/* Global cut: test rows rows[nr] (pixel indices into pts), refinement in rounds
+ * that split at most floor(growth * |cut|) nodes of error above eps, largest
+ * errors first, until no node qualifies or |cut| = max_cut.  cut[max_cut] receives
+ * tree node ids in leaf order, *cut_size_host its size. */
+lt_status lt_build_global_cut(lt_ctx* ctx, const lt_tree* tree, const float* pts, int64_t m,
+                              const float* vpls, const int32_t* rows, int64_t nr, float eps,
+                              int32_t max_cut, float growth, float d_min, int32_t* cut,
+                              int32_t* cut_size_host);
+/* Forest of the cut (layout in lt_frame).  forest[(2C-1)*8], level_off[max_levels+2],
+ * level_nodes[C-1]; *height_host receives H. */
+lt_status lt_cut_forest(lt_ctx* ctx, const lt_tree* tree, const int32_t* cut, int32_t C,
+                        int32_t* forest, int32_t* level_off, int32_t max_levels,
+                        int32_t* level_nodes, int32_t* height_host);
+
+/* ---- Step 2 (Sec. 3): matrix slicing -------------------------------------- */
+/* k-means of the features (p, w n) into S slices, `iters` Lloyd rounds from the
+ * Morton-rank seeds; row_perm[m] lists pixels slice by slice (ascending pixel index
+ * inside a slice), slice_off[S+1] delimits the slices. */
+lt_status lt_make_slices(lt_ctx* ctx, const float* pts, int64_t m, int32_t S, int32_t iters,
+                         float normal_weight, int32_t* row_perm, int32_t* slice_off);
+/* pts_out[3][m][4] = pts with rows permuted by row_perm. */
+lt_status lt_permute_points(lt_ctx* ctx, const float* pts, int64_t m, const int32_t* row_perm,
+                            float* pts_out);
+
+/* ---- Steps 3-5 (Sec. 4, Sec. 5, Sec. 3 step 5): one frame ------------------ */
+/* Pass 1 + light coarsening (Sec. 4, Eq. 2): per slice, k_c rows per cut node drawn
+ * with Philox (counter t, c, slice, 1), entries evaluated, sibling pairs merged
+ * while cost = eps + cost(q) < tau * S_hat.  Writes ncol, col_node, g, the pass-1
+ * keys/values (n1 = cnt).  A slice whose entries exceed its capacity latches
+ * LT_ELIMIT. */
+lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate, float tau, float d_min,
+                          uint64_t seed, lt_samples* smp);
+/* Pass 2 (Sec. 5, Eq. 3): draws (column by the integer CDF of `weights` or of g when
+ * weights is NULL, row uniform) with Philox (t, 0, slice, 2), keeping the first
+ * ceil(rate m' n') - n1 new entries.  Appends keys (values undefined until
+ * lt_eval_entries) and sets cnt. */
+lt_status lt_sample_pass2(lt_ctx* ctx, const lt_frame* f, const float* weights, float rate,
+                          uint64_t seed, lt_samples* smp);
+/* Evaluate the entries n1[s] .. cnt[s]-1 of every slice (shadow rays inside). */
+lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min, lt_samples* smp);
+/* Instrumentation (no counterpart in the paper): re-runs the evaluation of the same
+ * entries without storing values and returns in stats_host[4] the entries, the shadow
+ * rays cast (entries with a positive unoccluded value), the grid cells visited and
+ * the box slab tests made.  Synchronous. */
+lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, const lt_samples* smp,
+                        int64_t* stats_host);
+/* Masked ALS at rank r, `iters` sweeps (U-step then V-step), ridge lam_rel
+ * trace(G)/r, V0 from Philox (k, j, slice, 3); float32 Cholesky with a float64
+ * retry when min/max pivot^2 < 1e-6. */
+lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
+                      float lam_rel, uint64_t seed, lt_factors* uv);
+/* img[row_perm[slice_off[s] + i]] = max(0, u_i . (V_s^T w_s)); w NULL = all ones
+ * (the column sum, Sec. 3 step 5), else w[S][C]. */
+lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
+                    const float* w, const int32_t* row_perm, float* img);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LT_H_ */

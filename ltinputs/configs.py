@@ -23,7 +23,7 @@ _BASE = dict(
     light_size=0.2,
     eps_cut=0.05,
     tau=0.02,
-    lam_rel=1e-4,
+    lam_rel=1e-2,
     d_min=0.01,
     slice_feature_normal_weight=0.3,
     kmeans_iters=10,

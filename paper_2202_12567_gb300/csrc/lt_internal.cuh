@@ -1,0 +1,354 @@
+// Internal device code shared by the translation units of liblt (sm_103a).
+//
+// Philox4x32-10 (Salmon et al., SC'11), the uniform-grid shadow-ray test, the
+// entry model A(i, j) of the lighting matrix (Sec. 3; the shading formula is the
+// reading documented in include/lt.h), block-wide scans and the context struct.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lt.h"
+
+namespace ltk {
+
+constexpr float kRayOffset = 1e-4f;
+constexpr float kTMin = 1e-4f;
+constexpr float kTMax = 1.0f - 1e-4f;
+constexpr float kInvPi = 0.318309886183790672f;
+constexpr uint32_t kTagPass1 = 1, kTagPass2 = 2, kTagAlsInit = 3;
+
+// ----------------------------------------------------------------- Philox4x32-10
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+#else
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+#endif
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        if (r < 9) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+    }
+    return {c0, c1, c2, c3};
+}
+
+// floor(w * size / 2^32)
+__host__ __device__ inline uint32_t uniform_index(uint32_t w, uint32_t size) {
+    return (uint32_t)(((uint64_t)w * (uint64_t)size) >> 32);
+}
+
+// ----------------------------------------------------------------- small vector helpers
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// ----------------------------------------------------------------- occluder grid
+// Uniform grid of R^3 cells over the boxes' bounds; cell c lists the boxes that
+// overlap it (expanded by a small margin so that rounding at cell faces cannot hide
+// a box from a ray that the exact test would block).
+struct Grid {
+    const float* box;        // [nb][6]
+    const int32_t* cell_off; // [R^3 + 1]
+    const int32_t* cell_box; // [cell_off[R^3]]
+    int nb;
+    int R;
+    float lo[3];
+    float cell[3];
+    float inv_cell[3];
+};
+
+// Closed-box slab test of o + t D over t in [kTMin, kTMax].
+__device__ __forceinline__ bool slab_hit(const float* __restrict__ b, float3 o, float3 inv, int par) {
+    float tn = kTMin, tf = kTMax;
+    const float2 b01 = __ldg(reinterpret_cast<const float2*>(b));
+    const float2 b23 = __ldg(reinterpret_cast<const float2*>(b) + 1);
+    const float2 b45 = __ldg(reinterpret_cast<const float2*>(b) + 2);
+    const float lo0 = b01.x, lo1 = b01.y, lo2 = b23.x, hi0 = b23.y, hi1 = b45.x, hi2 = b45.y;
+    if (par & 1) {
+        if (o.x < lo0 || o.x > hi0) return false;
+    } else {
+        const float ta = (lo0 - o.x) * inv.x, tb = (hi0 - o.x) * inv.x;
+        tn = fmaxf(tn, fminf(ta, tb));
+        tf = fminf(tf, fmaxf(ta, tb));
+    }
+    if (par & 2) {
+        if (o.y < lo1 || o.y > hi1) return false;
+    } else {
+        const float ta = (lo1 - o.y) * inv.y, tb = (hi1 - o.y) * inv.y;
+        tn = fmaxf(tn, fminf(ta, tb));
+        tf = fminf(tf, fmaxf(ta, tb));
+    }
+    if (par & 4) {
+        if (o.z < lo2 || o.z > hi2) return false;
+    } else {
+        const float ta = (lo2 - o.z) * inv.z, tb = (hi2 - o.z) * inv.z;
+        tn = fmaxf(tn, fminf(ta, tb));
+        tf = fminf(tf, fmaxf(ta, tb));
+    }
+    return tn <= tf;
+}
+
+// Work done by the traversal (instrumentation of the ALU roofline).
+struct WorkCount {
+    int cells = 0;
+    int boxes = 0;
+};
+
+// Any-hit test of the segment o -> e (t in (kTMin, kTMax)) by a 3-D DDA walk.
+// The walk is bounded by the number of cells a straight segment can cross.
+template <bool COUNT = false>
+__device__ inline bool seg_blocked(const Grid& g, float3 o, float3 e, WorkCount* wc = nullptr) {
+    if (g.nb == 0) return false;
+    const float3 D = e - o;
+    const int par = (D.x == 0.f ? 1 : 0) | (D.y == 0.f ? 2 : 0) | (D.z == 0.f ? 4 : 0);
+    const float3 inv = make_float3((par & 1) ? 0.f : 1.f / D.x, (par & 2) ? 0.f : 1.f / D.y,
+                                   (par & 4) ? 0.f : 1.f / D.z);
+    const int R = g.R;
+    float t0 = kTMin, t1 = kTMax;
+    const float oa[3] = {o.x, o.y, o.z};
+    const float ia[3] = {inv.x, inv.y, inv.z};
+    const float da[3] = {D.x, D.y, D.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float lo = g.lo[a], hi = g.lo[a] + R * g.cell[a];
+        if (par & (1 << a)) {
+            if (oa[a] < lo || oa[a] > hi) return false;
+        } else {
+            const float ta = (lo - oa[a]) * ia[a], tb = (hi - oa[a]) * ia[a];
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        }
+    }
+    if (t0 > t1) return false;
+    int c[3], st[3];
+    float tn[3], td[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float x = oa[a] + t0 * da[a];
+        int ci = (int)floorf((x - g.lo[a]) * g.inv_cell[a]);
+        ci = ci < 0 ? 0 : (ci >= R ? R - 1 : ci);
+        c[a] = ci;
+        if (par & (1 << a)) {
+            st[a] = 0;
+            tn[a] = 3.0e38f;
+            td[a] = 3.0e38f;
+        } else {
+            st[a] = da[a] > 0.f ? 1 : -1;
+            const float bnd = g.lo[a] + (float)(ci + (st[a] > 0 ? 1 : 0)) * g.cell[a];
+            tn[a] = (bnd - oa[a]) * ia[a];
+            td[a] = g.cell[a] * fabsf(ia[a]);
+        }
+    }
+    const int max_steps = 3 * R + 3;
+    for (int it = 0; it < max_steps; ++it) {
+        const int cell = (c[2] * R + c[1]) * R + c[0];
+        const int b0 = __ldg(g.cell_off + cell), b1 = __ldg(g.cell_off + cell + 1);
+        if (COUNT) ++wc->cells;
+        for (int k = b0; k < b1; ++k) {
+            const int bi = __ldg(g.cell_box + k);
+            if (COUNT) ++wc->boxes;
+            if (slab_hit(g.box + 6 * bi, o, inv, par)) return true;
+        }
+        int a = 0;
+        if (tn[1] < tn[a]) a = 1;
+        if (tn[2] < tn[a]) a = 2;
+        if (tn[a] > t1) break;
+        c[a] += st[a];
+        if (c[a] < 0 || c[a] >= R) break;
+        tn[a] += td[a];
+    }
+    return false;
+}
+
+// ----------------------------------------------------------------- entry model
+// Phong lobe: cos a = R(wi) . wo = 2 (n.wi)(n.wo) - wi.wo.  The lobe raises cos a to
+// the exponent e (up to 100), which multiplies the relative rounding error of cos a
+// by e; so cos a - 1 is formed in double from the float inputs and the power is taken
+// as exp(e log1p(cos a - 1)).
+__device__ __forceinline__ float brdf(float alb, float gloss, float3 n, float3 wi, float3 wo) {
+    if (!(gloss > 0.f)) return alb * kInvPi;
+    const double ni = (double)n.x * wi.x + (double)n.y * wi.y + (double)n.z * wi.z;
+    const double no = (double)n.x * wo.x + (double)n.y * wo.y + (double)n.z * wo.z;
+    const double io = (double)wi.x * wo.x + (double)wi.y * wo.y + (double)wi.z * wo.z;
+    const double cm1 = 2.0 * ni * no - io - 1.0;
+    const float lobe = cm1 > -1.0 ? expf(gloss * log1pf((float)cm1)) : 0.f;
+    return 0.5f * alb * kInvPi + 0.5f * alb * (gloss + 2.f) * (0.5f * kInvPi) * lobe;
+}
+
+struct PointRec {
+    float4 a, b, c;   // [p albedo] [n gloss] [wo 0]
+};
+
+__device__ __forceinline__ PointRec load_rec(const float4* __restrict__ planes, int64_t count, int64_t i) {
+    PointRec r;
+    r.a = __ldg(planes + i);
+    r.b = __ldg(planes + count + i);
+    r.c = __ldg(planes + 2 * count + i);
+    return r;
+}
+
+// Unoccluded part flux * f_p * f_q * G (0 when a cosine is not positive).
+__device__ __forceinline__ float unoccluded(const PointRec& P, const PointRec& L, float dmin2) {
+    const float3 d = f3(L.a) - f3(P.a);
+    const float dist2 = dot3(d, d);
+    const float inv = 1.f / sqrtf(fmaxf(dist2, 1e-30f));
+    const float3 w = inv * d;
+    const float cp = dot3(f3(P.b), w);
+    const float cq = -dot3(f3(L.b), w);
+    if (!(cp > 0.f && cq > 0.f)) return 0.f;
+    const float G = cp * cq / fmaxf(dist2, dmin2);
+    const float fp = brdf(P.a.w, P.b.w, f3(P.b), w, f3(P.c));
+    const float fq = brdf(L.a.w, L.b.w, f3(L.b), f3(L.c), make_float3(-w.x, -w.y, -w.z));
+    return L.c.w * fp * fq * G;
+}
+
+// scale * A(i, j): the unoccluded value, then the shadow ray where it is positive.
+template <bool COUNT = false>
+__device__ __forceinline__ float entry_value(const PointRec& P, const PointRec& L, float scale, float dmin2,
+                                             const Grid& g, WorkCount* wc = nullptr, int* rays = nullptr) {
+    float v = unoccluded(P, L, dmin2) * scale;
+    if (v > 0.f) {
+        const float3 o = f3(P.a) + kRayOffset * f3(P.b);
+        const float3 e = f3(L.a) + kRayOffset * f3(L.b);
+        if (COUNT) ++*rays;
+        if (seg_blocked<COUNT>(g, o, e, wc)) v = 0.f;
+    }
+    return v;
+}
+
+// ----------------------------------------------------------------- block scans
+// Exclusive prefix sum over the block (blockDim.x a multiple of 32, <= 1024).
+// `warp_sums` must hold 32 ints of shared memory.  Returns the prefix; *total gets
+// the block sum.  Every thread of the block must call it.
+template <typename T>
+__device__ inline T block_exclusive_scan(T x, T* warp_sums, T* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T v = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        T s = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const T before = (wid > 0 ? warp_sums[wid - 1] : T(0)) + v - x;
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+template <typename T>
+__device__ inline T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ inline float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Latch the first error code into the status word.
+__device__ inline void latch(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
+
+// First index in [0, n) with a[idx] >= x (a ascending).
+template <typename T>
+__device__ __forceinline__ int lower_bound(const T* a, int n, T x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+}  // namespace ltk
+
+// ----------------------------------------------------------------- context
+enum ScratchSlot {
+    SCR_P1_PLAN = 0,    // per slice per forest node: k, cap, off, cnt, cost, state
+    SCR_P1_STORE,       // node storage (rows, v0, v1)
+    SCR_P1_SLICE,       // per slice totals and bases
+    SCR_BITMAP,         // per slice observed-entry bitmaps (row-major and column-major)
+    SCR_OMEGA,          // CSR / CSC of the observed entries
+    SCR_ALS,            // per-slice statistics for ALS
+    SCR_MISC,           // small reductions
+    SCR_SORT,           // sort keys
+    SCR_CUT,            // global-cut work arrays
+    SCR_NSLOTS
+};
+
+struct lt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int32_t* d_status = nullptr;
+    int32_t* h_status = nullptr;
+    std::string err;
+    // occluder grid
+    float* d_boxes = nullptr;
+    int32_t* d_cell_off = nullptr;
+    int32_t* d_cell_box = nullptr;
+    ltk::Grid grid{};
+    // scratch
+    void* scr[SCR_NSLOTS] = {};
+    size_t scr_size[SCR_NSLOTS] = {};
+    int num_sms = 0;
+    int64_t launches = 0;   // kernels launched through this context
+};
+
+// Helpers implemented in lt_api.cu.
+lt_status lt_fail(lt_ctx* ctx, lt_status code, const std::string& msg);
+lt_status lt_cuda_check(lt_ctx* ctx, cudaError_t e, const char* what);
+void* lt_scratch(lt_ctx* ctx, int slot, size_t bytes, lt_status* st);
+
+#define LT_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e__ = (call);                                    \
+        if (e__ != cudaSuccess) return lt_cuda_check(ctx, e__, #call); \
+    } while (0)
+
+#define LT_LAUNCH_CHECK(ctx, name)                                         \
+    do {                                                                   \
+        ++(ctx)->launches;                                                 \
+        cudaError_t e__ = cudaGetLastError();                              \
+        if (e__ != cudaSuccess) return lt_cuda_check(ctx, e__, name);      \
+    } while (0)

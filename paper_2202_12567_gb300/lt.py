@@ -1,0 +1,363 @@
+"""Thin Python binding of liblt (include/lt.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does no
+computation of its own: device memory comes from PyTorch tensors, whose raw
+pointers are handed to the library, and every step runs in the library's CUDA
+kernels.  Importing this module loads liblt.so and fails loudly when it is
+missing; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblt.so")
+
+LT_OK, LT_EINVAL, LT_ENOMEM, LT_ECUDA, LT_ELIMIT, LT_ENUMERIC = 0, 1, 2, 3, 4, 5
+
+
+class LtError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} failed with status {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+_f32 = ctypes.c_float
+_u64 = ctypes.c_uint64
+
+
+class lt_tree(ctypes.Structure):
+    _fields_ = [("n", _i64), ("order", _p), ("child", _p), ("parent", _p), ("range", _p), ("rep", _p),
+                ("I", _p), ("B", _p), ("aabb", _p)]
+
+
+class lt_frame(ctypes.Structure):
+    _fields_ = [("pts", _p), ("m", _i64), ("vpls", _p), ("n", _i64), ("slice_off", _p), ("S", _i32),
+                ("max_rows", _i32), ("tree", lt_tree), ("C", _i32), ("forest", _p), ("level_off", _p),
+                ("level_nodes", _p), ("H", _i32)]
+
+
+class lt_samples(ctypes.Structure):
+    _fields_ = [("ncol", _p), ("col_node", _p), ("g", _p), ("off", _p), ("key", _p), ("val", _p), ("n1", _p),
+                ("cnt", _p)]
+
+
+class lt_factors(ctypes.Structure):
+    _fields_ = [("r", _i32), ("U", _p), ("V", _p)]
+
+
+_SIGS = {
+    "lt_status_str": (ctypes.c_char_p, [_i32]),
+    "lt_last_error": (ctypes.c_char_p, [_p]),
+    "lt_create": (_i32, [ctypes.POINTER(_p), ctypes.c_int, _p]),
+    "lt_destroy": (_i32, [_p]),
+    "lt_sync": (_i32, [_p]),
+    "lt_status_word": (_p, [_p]),
+    "lt_launch_count": (_i64, [_p]),
+    "lt_debug_scratch": (_i32, [_p, _i32, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),
+    "lt_scene_upload": (_i32, [_p, _p, _i64, _i32]),
+    "lt_shadow_test": (_i32, [_p, _p, _p, _i64, _p]),
+    "lt_eval_pairs": (_i32, [_p, _p, _i64, _p, _i64, _p, _p, _p, _i64, _f32, _p]),
+    "lt_bruteforce": (_i32, [_p, _p, _i64, _p, _i64, _f32, _p]),
+    "lt_build_tree": (_i32, [_p, _p, _i64, ctypes.POINTER(lt_tree)]),
+    "lt_build_global_cut": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i64, _p, _p, _i64, _f32, _i32, _f32, _f32,
+                                   _p, ctypes.POINTER(_i32)]),
+    "lt_cut_forest": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i32, _p, _p, _i32, _p, ctypes.POINTER(_i32)]),
+    "lt_make_slices": (_i32, [_p, _p, _i64, _i32, _i32, _f32, _p, _p]),
+    "lt_permute_points": (_i32, [_p, _p, _i64, _p, _p]),
+    "lt_sample_pass1": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, _f32, _f32, _u64, ctypes.POINTER(lt_samples)]),
+    "lt_sample_pass2": (_i32, [_p, ctypes.POINTER(lt_frame), _p, _f32, _u64, ctypes.POINTER(lt_samples)]),
+    "lt_eval_entries": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples)]),
+    "lt_eval_stats": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples), _p]),
+    "lt_complete": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _u64,
+                           ctypes.POINTER(lt_factors)]),
+    "lt_render": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p,
+                         _p, _p]),
+}
+
+EXPORTED = sorted(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load liblt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"liblt.so not found at {path}: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """An lt_ctx handle on one device; calls run on ``stream`` (default: the current torch stream)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        self.lib = load()
+        self.device = device
+        torch.cuda.set_device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = _p()
+        self._check("lt_create", self.lib.lt_create(ctypes.byref(h), device, _p(self.stream.cuda_stream)))
+        self.h = h
+
+    def _check(self, fn, code):
+        if code != LT_OK:
+            msg = self.lib.lt_last_error(self.h).decode() if getattr(self, "h", None) else ""
+            raise LtError(fn, code, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lt_launch_count(ctx: Context) -> int:
+    return int(ctx.lib.lt_launch_count(ctx.h))
+
+
+class _DevBuf:
+    def __init__(self, ptr, nbytes):
+        self.__cuda_array_interface__ = dict(shape=(nbytes,), typestr="|u1", data=(ptr, False), version=3)
+
+
+def lt_debug_scratch(ctx: Context, slot: int) -> torch.Tensor:
+    """A uint8 view of scratch slot ``slot`` (debugging aid)."""
+    ptr, size = _p(), _i64()
+    ctx._check("lt_debug_scratch", ctx.lib.lt_debug_scratch(ctx.h, slot, ctypes.byref(ptr), ctypes.byref(size)))
+    if not ptr.value:
+        return torch.zeros(0, dtype=torch.uint8, device="cuda")
+    return torch.as_tensor(_DevBuf(ptr.value, size.value), device="cuda")
+
+
+def lt_sync(ctx: Context):
+    ctx._check("lt_sync", ctx.lib.lt_sync(ctx.h))
+
+
+def lt_scene_upload(ctx: Context, boxes: torch.Tensor, grid_res: int = 0):
+    boxes = boxes.contiguous()
+    ctx._boxes = boxes
+    ctx._check("lt_scene_upload", ctx.lib.lt_scene_upload(ctx.h, _ptr(boxes) if boxes.numel() else None,
+                                                          boxes.shape[0], grid_res))
+
+
+def lt_shadow_test(ctx: Context, org: torch.Tensor, end: torch.Tensor) -> torch.Tensor:
+    k = org.shape[0]
+    out = torch.empty(k, dtype=torch.uint8, device=org.device)
+    ctx._check("lt_shadow_test", ctx.lib.lt_shadow_test(ctx.h, _ptr(org), _ptr(end), k, _ptr(out)))
+    return out
+
+
+def lt_eval_pairs(ctx: Context, pts, vpls, rows, vpl, scale=None, d_min=0.01) -> torch.Tensor:
+    out = torch.empty(rows.shape[0], dtype=torch.float32, device=pts.device)
+    ctx._check("lt_eval_pairs", ctx.lib.lt_eval_pairs(ctx.h, _ptr(pts), pts.shape[1], _ptr(vpls), vpls.shape[1],
+                                                      _ptr(rows), _ptr(vpl), _ptr(scale), rows.shape[0], d_min,
+                                                      _ptr(out)))
+    return out
+
+
+def lt_bruteforce(ctx: Context, pts, vpls, d_min=0.01, out=None) -> torch.Tensor:
+    m = pts.shape[1]
+    img = torch.empty(m, dtype=torch.float32, device=pts.device) if out is None else out
+    ctx._check("lt_bruteforce", ctx.lib.lt_bruteforce(ctx.h, _ptr(pts), m, _ptr(vpls), vpls.shape[1], d_min,
+                                                      _ptr(img)))
+    return img
+
+
+class Tree:
+    """Device arrays of a light tree (see lt_tree)."""
+
+    def __init__(self, n: int, device):
+        N = 2 * n - 1
+        i32 = dict(dtype=torch.int32, device=device)
+        f32 = dict(dtype=torch.float32, device=device)
+        self.n = n
+        self.order = torch.empty(n, **i32)
+        self.child = torch.empty(N, 2, **i32)
+        self.parent = torch.empty(N, **i32)
+        self.range = torch.empty(N, 2, **i32)
+        self.rep = torch.empty(N, **i32)
+        self.I = torch.empty(N, **f32)
+        self.B = torch.empty(N, **f32)
+        self.aabb = torch.empty(N, 6, **f32)
+
+    def struct(self) -> lt_tree:
+        return lt_tree(self.n, _ptr(self.order), _ptr(self.child), _ptr(self.parent), _ptr(self.range),
+                       _ptr(self.rep), _ptr(self.I), _ptr(self.B), _ptr(self.aabb))
+
+
+def lt_build_tree(ctx: Context, vpls: torch.Tensor) -> Tree:
+    n = vpls.shape[1]
+    t = Tree(n, vpls.device)
+    s = t.struct()
+    ctx._check("lt_build_tree", ctx.lib.lt_build_tree(ctx.h, _ptr(vpls), n, ctypes.byref(s)))
+    return t
+
+
+def lt_build_global_cut(ctx: Context, tree: Tree, pts, vpls, rows, eps, max_cut, growth=0.5, d_min=0.01):
+    cut = torch.empty(max_cut, dtype=torch.int32, device=pts.device)
+    size = _i32(0)
+    s = tree.struct()
+    ctx._check("lt_build_global_cut", ctx.lib.lt_build_global_cut(
+        ctx.h, ctypes.byref(s), _ptr(pts), pts.shape[1], _ptr(vpls), _ptr(rows), rows.shape[0], eps, max_cut,
+        growth, d_min, _ptr(cut), ctypes.byref(size)))
+    return cut[:size.value].clone()
+
+
+def lt_cut_forest(ctx: Context, tree: Tree, cut: torch.Tensor, max_levels: int = 256):
+    C = cut.shape[0]
+    dev = cut.device
+    forest = torch.empty((2 * C - 1) * 8, dtype=torch.int32, device=dev)
+    level_off = torch.zeros(max_levels + 2, dtype=torch.int32, device=dev)
+    level_nodes = torch.empty(max(C - 1, 1), dtype=torch.int32, device=dev)
+    H = _i32(0)
+    s = tree.struct()
+    ctx._check("lt_cut_forest", ctx.lib.lt_cut_forest(ctx.h, ctypes.byref(s), _ptr(cut), C, _ptr(forest),
+                                                      _ptr(level_off), max_levels, _ptr(level_nodes),
+                                                      ctypes.byref(H)))
+    return forest, level_off, level_nodes, H.value
+
+
+def lt_make_slices(ctx: Context, pts, S, iters=10, normal_weight=0.3):
+    m = pts.shape[1]
+    perm = torch.empty(m, dtype=torch.int32, device=pts.device)
+    off = torch.empty(S + 1, dtype=torch.int32, device=pts.device)
+    ctx._check("lt_make_slices", ctx.lib.lt_make_slices(ctx.h, _ptr(pts), m, S, iters, normal_weight, _ptr(perm),
+                                                        _ptr(off)))
+    return perm, off
+
+
+def lt_permute_points(ctx: Context, pts, row_perm):
+    out = torch.empty_like(pts)
+    ctx._check("lt_permute_points", ctx.lib.lt_permute_points(ctx.h, _ptr(pts), pts.shape[1], _ptr(row_perm),
+                                                              _ptr(out)))
+    return out
+
+
+class Frame:
+    """The fixed inputs of a frame (lt_frame) and the tensors behind its pointers."""
+
+    def __init__(self, pts_s, vpls, slice_off, tree: Tree, cut, forest, level_off, level_nodes, H):
+        self.pts_s, self.vpls, self.slice_off, self.tree, self.cut = pts_s, vpls, slice_off, tree, cut
+        self.forest, self.level_off, self.level_nodes, self.H = forest, level_off, level_nodes, H
+        self.slice_off_host = slice_off.cpu().numpy().astype(np.int64)
+        self.sizes = np.diff(self.slice_off_host)
+        self.S = len(self.sizes)
+        self.C = int(cut.shape[0])
+        self.m = pts_s.shape[1]
+        self._s = lt_frame(_ptr(pts_s), self.m, _ptr(vpls), vpls.shape[1], _ptr(slice_off), self.S,
+                           int(self.sizes.max()), tree.struct(), self.C, _ptr(forest), _ptr(level_off),
+                           _ptr(level_nodes), H)
+
+    def struct(self) -> lt_frame:
+        return self._s
+
+
+class Samples:
+    """Per-slice observed entries (lt_samples) with a capacity layout for ``rate``."""
+
+    def __init__(self, frame: Frame, rate: float):
+        S, C = frame.S, frame.C
+        dev = frame.pts_s.device
+        caps = []
+        for ms in frame.sizes:
+            kappa = max(2.0, 0.3 * rate * ms)
+            k_sum = min(64, ms) * C if ms else 0
+            k_sum = min(k_sum, int(kappa * C + 2.5 * C + 1))
+            caps.append(2 * k_sum + int(math.ceil(rate * ms * C)) + 64)
+        off = np.concatenate([[0], np.cumsum(caps)]).astype(np.int64)
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.ncol = torch.zeros(S, **i32)
+        self.col_node = torch.zeros(S * C, **i32)
+        self.g = torch.zeros(S * C, dtype=torch.float32, device=dev)
+        self.off = torch.from_numpy(off).to(dev)
+        self.key = torch.zeros(int(off[-1]), dtype=torch.int32, device=dev)
+        self.val = torch.zeros(int(off[-1]), dtype=torch.float32, device=dev)
+        self.n1 = torch.zeros(S, **i32)
+        self.cnt = torch.zeros(S, **i32)
+        self.off_host = off
+        self._s = lt_samples(_ptr(self.ncol), _ptr(self.col_node), _ptr(self.g), _ptr(self.off), _ptr(self.key),
+                             _ptr(self.val), _ptr(self.n1), _ptr(self.cnt))
+
+    def struct(self) -> lt_samples:
+        return self._s
+
+    def slice(self, s: int):
+        """Host copies (rows, cols, vals, col_node, g) of slice s."""
+        o = int(self.off_host[s])
+        c = int(self.cnt[s].item())
+        n = int(self.ncol[s].item())
+        C = self.col_node.shape[0] // self.ncol.shape[0]
+        key = self.key[o:o + c].cpu().numpy().astype(np.uint32)
+        return (key >> 16).astype(np.int64), (key & 0xFFFF).astype(np.int64), self.val[o:o + c].cpu().numpy(), \
+            self.col_node[s * C:s * C + n].cpu().numpy(), self.g[s * C:s * C + n].cpu().numpy()
+
+
+class Factors:
+    def __init__(self, frame: Frame, r: int):
+        dev = frame.pts_s.device
+        self.r = r
+        self.U = torch.zeros(frame.m * r, dtype=torch.float32, device=dev)
+        self.V = torch.zeros(frame.S * frame.C * r, dtype=torch.float32, device=dev)
+        self._s = lt_factors(r, _ptr(self.U), _ptr(self.V))
+
+    def struct(self) -> lt_factors:
+        return self._s
+
+
+def lt_sample_pass1(ctx: Context, frame: Frame, smp: Samples, rate, tau, d_min, seed):
+    ctx._check("lt_sample_pass1", ctx.lib.lt_sample_pass1(ctx.h, ctypes.byref(frame.struct()), rate, tau, d_min,
+                                                          seed, ctypes.byref(smp.struct())))
+
+
+def lt_sample_pass2(ctx: Context, frame: Frame, smp: Samples, rate, seed, weights=None):
+    ctx._check("lt_sample_pass2", ctx.lib.lt_sample_pass2(ctx.h, ctypes.byref(frame.struct()), _ptr(weights), rate,
+                                                          seed, ctypes.byref(smp.struct())))
+
+
+def lt_eval_entries(ctx: Context, frame: Frame, smp: Samples, d_min):
+    ctx._check("lt_eval_entries", ctx.lib.lt_eval_entries(ctx.h, ctypes.byref(frame.struct()), d_min,
+                                                          ctypes.byref(smp.struct())))
+
+
+def lt_eval_stats(ctx: Context, frame: Frame, smp: Samples, d_min) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    ctx._check("lt_eval_stats", ctx.lib.lt_eval_stats(ctx.h, ctypes.byref(frame.struct()), d_min,
+                                                      ctypes.byref(smp.struct()), ctypes.cast(out, _p)))
+    return dict(entries=out[0], rays=out[1], cells=out[2], boxes=out[3])
+
+
+def lt_complete(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, lam_rel, seed):
+    ctx._check("lt_complete", ctx.lib.lt_complete(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
+                                                  iters, lam_rel, seed, ctypes.byref(uv.struct())))
+
+
+def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, img, w=None):
+    ctx._check("lt_render", ctx.lib.lt_render(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
+                                              ctypes.byref(uv.struct()), _ptr(w), _ptr(row_perm), _ptr(img)))

@@ -1,0 +1,105 @@
+"""One scene, one camera: setup (tree, global cut, forest, slices) and frames.
+
+A frame is the hot path of the method: pass 1 with coarsening (Sec. 4), pass 2
+(Sec. 5), evaluation of the pass-2 entries, completion of every slice and the
+factorised render (Sec. 3 step 5).  Every step is a liblt call; this class only
+owns the tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import lt
+
+
+def test_rows(width: int, height: int, block: int = 8) -> np.ndarray:
+    """One pixel per block x block tile (offset block/2): the rows that drive the global cut."""
+    ys = np.arange(block // 2, height, block)
+    xs = np.arange(block // 2, width, block)
+    if ys.size == 0:
+        ys = np.array([height // 2])
+    if xs.size == 0:
+        xs = np.array([width // 2])
+    gy, gx = np.meshgrid(ys, xs, indexing="ij")
+    return (gy * width + gx).ravel()
+
+
+class Renderer:
+    def __init__(self, scene, cfg: dict, device: int = 0, ctx: lt.Context | None = None):
+        self.cfg = dict(cfg)
+        self.scene = scene
+        self.dev = torch.device("cuda", device)
+        self.ctx = ctx if ctx is not None else lt.Context(device)
+        self.pts = torch.from_numpy(np.ascontiguousarray(scene.points)).to(self.dev)
+        self.vpls = torch.from_numpy(np.ascontiguousarray(scene.vpls)).to(self.dev)
+        self.boxes = torch.from_numpy(np.ascontiguousarray(scene.boxes)).to(self.dev).reshape(-1, 6)
+        lt.lt_scene_upload(self.ctx, self.boxes)
+        self.frame = None
+
+    # ---------------------------------------------------------------- setup (a0)
+    def setup(self, cut=None, row_perm=None, slice_off=None):
+        """Tree, global cut, forest and slices; ``cut``/``row_perm``/``slice_off`` may be
+        given (e.g. from another implementation) instead of being computed."""
+        cfg = self.cfg
+        ctx = self.ctx
+        self.tree = lt.lt_build_tree(ctx, self.vpls)
+        if cut is None:
+            rows = torch.from_numpy(test_rows(self.scene.width, self.scene.height).astype(np.int32)).to(self.dev)
+            cut = lt.lt_build_global_cut(ctx, self.tree, self.pts, self.vpls, rows, cfg["eps_cut"], cfg["max_cut"],
+                                         cfg.get("cut_growth", 0.5), cfg["d_min"])
+        else:
+            cut = torch.as_tensor(np.asarray(cut), dtype=torch.int32).to(self.dev)
+        self.cut = cut
+        forest, level_off, level_nodes, H = lt.lt_cut_forest(ctx, self.tree, cut)
+        if row_perm is None:
+            row_perm, slice_off = lt.lt_make_slices(ctx, self.pts, cfg["n_slices"], cfg["kmeans_iters"],
+                                                    cfg["slice_feature_normal_weight"])
+        else:
+            row_perm = torch.as_tensor(np.asarray(row_perm), dtype=torch.int32).to(self.dev)
+            slice_off = torch.as_tensor(np.asarray(slice_off), dtype=torch.int32).to(self.dev)
+        self.row_perm, self.slice_off = row_perm, slice_off
+        self.pts_s = lt.lt_permute_points(ctx, self.pts, row_perm)
+        self.frame = lt.Frame(self.pts_s, self.vpls, slice_off, self.tree, cut, forest, level_off, level_nodes, H)
+        self.smp = lt.Samples(self.frame, cfg["rate"])
+        self.uv = lt.Factors(self.frame, cfg["rank"])
+        self.img = torch.zeros(self.frame.m, dtype=torch.float32, device=self.dev)
+        lt.lt_sync(ctx)
+        return self
+
+    # ---------------------------------------------------------------- frame stages
+    def pass1(self, seed):
+        c = self.cfg
+        lt.lt_sample_pass1(self.ctx, self.frame, self.smp, c["rate"], c["tau"], c["d_min"], seed)
+
+    def pass2(self, seed, weights=None):
+        lt.lt_sample_pass2(self.ctx, self.frame, self.smp, self.cfg["rate"], seed, weights)
+
+    def evaluate(self):
+        lt.lt_eval_entries(self.ctx, self.frame, self.smp, self.cfg["d_min"])
+
+    def complete(self, seed):
+        c = self.cfg
+        lt.lt_complete(self.ctx, self.frame, self.smp, self.uv, c["als_iters"], c["lam_rel"], seed)
+
+    def render_image(self, w=None):
+        lt.lt_render(self.ctx, self.frame, self.smp, self.uv, self.row_perm, self.img, w)
+
+    def render(self, seed=None, weights=None, sync=True):
+        """One frame: pass 1, pass 2, entry evaluation, completion, image."""
+        seed = self.cfg["frame_seed"] if seed is None else seed
+        self.pass1(seed)
+        self.pass2(seed, weights)
+        self.evaluate()
+        self.complete(seed)
+        self.render_image()
+        if sync:
+            lt.lt_sync(self.ctx)
+        return self.img
+
+    def bruteforce(self, out=None):
+        return lt.lt_bruteforce(self.ctx, self.pts, self.vpls, self.cfg["d_min"], out)
+
+    def rays(self) -> int:
+        """Shadow-ray-bearing entries of the last frame (pass-1 tests are counted in pass 1)."""
+        return int(self.smp.cnt.sum().item())

@@ -1,0 +1,350 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Stage-isolated: every stage is fed exactly the oracle's inputs for that stage
+(cut, slices, pass-1 entries, observed set) and compared with the oracle's output:
+bit-exact for index work (tree, forest, draws, coarsened cuts), 1e-5 relative for
+sampled entries, <= 1e-4 of shadow rays disagreeing, 1e-3 relative for images of
+completed factors after the same iterations.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from ltinputs import get_config, make_scene
+from oracle import als as o_als, bruteforce, pass1 as o_pass1, pass2 as o_pass2, pipeline, render as o_render
+from oracle import shading, slices as o_slices, tree as o_tree
+
+pytestmark = pytest.mark.gpu
+
+ENTRY_RTOL = 1e-5
+IMAGE_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def lt():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2202_12567_gb300 import lt as _lt
+    _lt.load()
+    return _lt
+
+
+@pytest.fixture(scope="module")
+def ctx(lt):
+    return lt.Context(0)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    cfg = get_config("room64_vpl1k_2box", max_cut=256)
+    sc = make_scene(cfg)
+    st = pipeline.setup(sc, cfg)
+    return cfg, sc, st
+
+
+@pytest.fixture(scope="module")
+def medium_scene():
+    cfg = get_config("room256_vpl16k_200box")
+    return cfg, make_scene(cfg)
+
+
+def _cuda(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+# --------------------------------------------------------------------------- visibility
+@pytest.mark.parametrize("nb,grid_res", [(2, 0), (200, 0), (200, 5), (1000, 0)])
+def test_shadow_rays_match_all_boxes(lt, ctx, nb, grid_res):
+    rng = np.random.default_rng(nb + grid_res)
+    cfg = get_config("room256_vpl16k_200box", n_small_boxes=nb, n_big_boxes=0, width=8, height=8, n_vpl=8)
+    boxes = make_scene(cfg).boxes
+    k = 200_000
+    o = rng.uniform(0, 1, (k, 3)).astype(np.float32)
+    e = rng.uniform(0, 1, (k, 3)).astype(np.float32)
+    lt.lt_scene_upload(ctx, _cuda(boxes), grid_res)
+    got = lt.lt_shadow_test(ctx, _cuda(o), _cuda(e)).cpu().numpy().astype(bool)
+    exp = shading.segment_blocked(o.astype(np.float64), e.astype(np.float64), boxes)
+    assert np.mean(got != exp) <= 1e-4
+    assert 0.01 < exp.mean() < 0.99
+
+
+def test_shadow_hand_cases(lt, ctx):
+    box = np.array([[0.4, 0.4, 0.4, 0.6, 0.6, 0.6]], dtype=np.float32)
+    cases = [((0.5, 0.5, 0.0), (0.5, 0.5, 1.0), 1), ((0.5, 0.7, 0.0), (0.5, 0.7, 1.0), 0),
+             ((0.5, 0.5, 0.0), (0.5, 0.5, 0.3), 0), ((0.3, 0.3, 0.3), (0.7, 0.7, 0.7), 1),
+             ((0.2, 0.8, 0.5), (0.55, 0.8, 0.5), 0), ((0.5, 0.5, 0.5), (0.5, 0.5, 0.9), 1)]
+    lt.lt_scene_upload(ctx, _cuda(box))
+    o = np.array([c[0] for c in cases], dtype=np.float32)
+    e = np.array([c[1] for c in cases], dtype=np.float32)
+    got = lt.lt_shadow_test(ctx, _cuda(o), _cuda(e)).cpu().numpy()
+    assert got.tolist() == [c[2] for c in cases]
+
+
+# --------------------------------------------------------------------------- entries
+@pytest.mark.parametrize("glossy", [0.0, 0.3])
+def test_eval_pairs_match_oracle(lt, ctx, glossy):
+    cfg = get_config("room256_vpl16k_200box", width=64, height=64, n_vpl=2048, glossy_frac=glossy)
+    sc = make_scene(cfg)
+    rng = np.random.default_rng(3)
+    k = 300_000
+    rows = rng.integers(0, sc.m, k).astype(np.int32)
+    vpl = rng.integers(0, sc.n, k).astype(np.int32)
+    scale = rng.uniform(0.5, 2.0, k).astype(np.float32)
+    lt.lt_scene_upload(ctx, _cuda(sc.boxes))
+    got = lt.lt_eval_pairs(ctx, _cuda(sc.points), _cuda(sc.vpls), _cuda(rows), _cuda(vpl), _cuda(scale),
+                           cfg["d_min"]).cpu().numpy().astype(np.float64)
+    exp = shading.vpl_entries(sc.points, sc.vpls, rows, vpl, sc.boxes, cfg["d_min"]) * scale.astype(np.float64)
+    # visibility disagreements (one side zero, the other not) within the shadow-ray bound
+    vis_dis = ((got == 0) != (exp == 0)) & (np.maximum(got, exp) > 1e-12 * exp.max())
+    assert vis_dis.mean() <= 1e-4
+    ok = ~vis_dis
+    err = np.abs(got[ok] - exp[ok])
+    tol = ENTRY_RTOL * np.abs(exp[ok]) + 1e-7 * exp.max() * 1e-3
+    assert np.all(err <= tol), f"max rel err {np.max(err / np.maximum(np.abs(exp[ok]), 1e-30))}"
+
+
+def test_bruteforce_matches_oracle(lt, ctx, tiny):
+    cfg, sc, st = tiny
+    lt.lt_scene_upload(ctx, _cuda(sc.boxes))
+    img = lt.lt_bruteforce(ctx, _cuda(sc.points), _cuda(sc.vpls), cfg["d_min"]).cpu().numpy()
+    ref = bruteforce.render(sc.points, sc.vpls, sc.boxes, cfg["d_min"])
+    assert bruteforce.rel_rmse(img, ref) <= 1e-5
+    assert np.max(np.abs(img - ref) / np.maximum(ref, 1e-3 * ref.max())) <= 1e-3
+
+
+def test_bruteforce_medium_sampled_rows(lt, ctx, medium_scene):
+    cfg, sc = medium_scene
+    lt.lt_scene_upload(ctx, _cuda(sc.boxes))
+    img = lt.lt_bruteforce(ctx, _cuda(sc.points), _cuda(sc.vpls), cfg["d_min"]).cpu().numpy()
+    rows = np.random.default_rng(0).choice(sc.m, 48, replace=False)
+    ref = bruteforce.render_rows(sc.points, sc.vpls, sc.boxes, rows, cfg["d_min"])
+    np.testing.assert_allclose(img[rows], ref, rtol=1e-3)
+
+
+# --------------------------------------------------------------------------- setup
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (7, 2), (1000, 3), (16384, 4)])
+def test_tree_bit_exact(lt, ctx, n, seed):
+    sc = make_scene(get_config("room256_vpl16k_200box", n_vpl=n, width=8, height=8), seed=seed)
+    ref = o_tree.build(sc.vpls)
+    t = lt.lt_build_tree(ctx, _cuda(sc.vpls))
+    assert np.array_equal(t.order.cpu().numpy(), ref.order)
+    N = 2 * n - 1
+    assert np.array_equal(t.child.cpu().numpy().reshape(N, 2), ref.child)
+    assert np.array_equal(t.parent.cpu().numpy(), ref.parent)
+    rng = t.range.cpu().numpy().reshape(N, 2)
+    assert np.array_equal(rng[:, 0], ref.first) and np.array_equal(rng[:, 1], ref.last)
+    assert np.array_equal(t.rep.cpu().numpy(), ref.rep)
+    assert np.array_equal(t.I.cpu().numpy(), ref.I)
+    bb = t.aabb.cpu().numpy().reshape(N, 6)
+    assert np.array_equal(bb[:, :3], ref.lo) and np.array_equal(bb[:, 3:], ref.hi)
+    np.testing.assert_allclose(t.B.cpu().numpy(), ref.B, rtol=1e-6)
+
+
+def test_forest_matches_oracle(lt, ctx, tiny):
+    cfg, sc, st = tiny
+    t = lt.lt_build_tree(ctx, _cuda(sc.vpls))
+    forest, level_off, level_nodes, H = lt.lt_cut_forest(ctx, t, _cuda(st["cut"].astype(np.int32)))
+    fo = forest.cpu().numpy().reshape(-1, 8)
+    ref = st["forest"]
+    assert np.array_equal(fo[:, 0], ref.node)
+    assert np.array_equal(fo[:, 1:3], ref.child)
+    assert np.array_equal(fo[:, 3], ref.parent)
+
+
+def test_global_cut_agrees_with_oracle(lt, ctx, tiny):
+    cfg, sc, st = tiny
+    from paper_2202_12567_gb300.renderer import test_rows
+    lt.lt_scene_upload(ctx, _cuda(sc.boxes))
+    t = lt.lt_build_tree(ctx, _cuda(sc.vpls))
+    rows = _cuda(test_rows(sc.width, sc.height).astype(np.int32))
+    cut = lt.lt_build_global_cut(ctx, t, _cuda(sc.points), _cuda(sc.vpls), rows, cfg["eps_cut"], cfg["max_cut"],
+                                 0.5, cfg["d_min"]).cpu().numpy()
+    ref = st["cut"]
+    tr = st["tree"]
+    cover = np.zeros(tr.n, dtype=int)
+    for c in cut:
+        cover[tr.first[c]:tr.last[c] + 1] += 1
+    assert np.all(cover == 1) and len(cut) == len(ref)
+    agree = len(set(cut.tolist()) & set(ref.tolist())) / len(ref)
+    assert agree >= 0.95, agree
+
+
+def test_slices_agree_with_oracle(lt, ctx, tiny):
+    cfg, sc, st = tiny
+    perm, off = lt.lt_make_slices(ctx, _cuda(sc.points), cfg["n_slices"], cfg["kmeans_iters"],
+                                  cfg["slice_feature_normal_weight"])
+    perm, off = perm.cpu().numpy(), off.cpu().numpy()
+    lab = np.empty(sc.m, dtype=np.int64)
+    for s in range(len(off) - 1):
+        lab[perm[off[s]:off[s + 1]]] = s
+    ref_lab = np.empty(sc.m, dtype=np.int64)
+    for s in range(len(st["slice_off"]) - 1):
+        ref_lab[st["row_perm"][st["slice_off"][s]:st["slice_off"][s + 1]]] = s
+    assert np.mean(lab == ref_lab) >= 0.99
+    # the permutation is slice-contiguous and ascending inside each slice
+    assert sorted(perm.tolist()) == list(range(sc.m))
+    for s in range(len(off) - 1):
+        assert np.all(np.diff(perm[off[s]:off[s + 1]]) > 0)
+
+
+# --------------------------------------------------------------------------- frame stages
+@pytest.fixture(scope="module")
+def tiny_gpu(lt, tiny):
+    from paper_2202_12567_gb300.renderer import Renderer
+    cfg, sc, st = tiny
+    R = Renderer(sc, cfg, device=0).setup(cut=st["cut"], row_perm=st["row_perm"], slice_off=st["slice_off"])
+    seed = cfg["frame_seed"]
+    R.pass1(seed)
+    lt.lt_sync(R.ctx)
+    p1 = {s: (R.smp.slice(s)) for s in range(R.frame.S)}
+    ores = {}
+    for s in range(R.frame.S):
+        ores[s] = pipeline.run_slice(st, sc, cfg, s, seed)
+    return cfg, sc, st, R, p1, ores
+
+
+def _entry_dict(rows, cols, vals):
+    return dict(zip((np.asarray(rows) * 65536 + np.asarray(cols)).tolist(), np.asarray(vals).tolist()))
+
+
+def test_pass1_coarsened_cut_and_entries(tiny_gpu):
+    cfg, sc, st, R, p1, ores = tiny_gpu
+    n_exact = 0
+    for s, (rows, cols, vals, col_node, g) in p1.items():
+        o = ores[s].p1
+        if not np.array_equal(col_node, o.col_node):
+            # a different decision is acceptable only on a near-tie of cost and threshold
+            margins = [abs(cf - thr) / max(thr, 1e-30) for (_, _, cf, thr, *_rest) in o.log]
+            assert min(margins) < 1e-4, f"slice {s}: coarsened cut differs without a near tie"
+            continue
+        n_exact += 1
+        got, exp = _entry_dict(rows, cols, vals), _entry_dict(o.rows, o.cols, o.vals)
+        assert got.keys() == exp.keys(), f"slice {s}"
+        k = sorted(exp)
+        gv, ev = np.array([got[x] for x in k]), np.array([exp[x] for x in k])
+        assert np.all(np.abs(gv - ev) <= ENTRY_RTOL * np.abs(ev) + 1e-12), f"slice {s}"
+        np.testing.assert_allclose(g, o.g, rtol=1e-4, atol=1e-9)
+    assert n_exact >= len(p1) - 1
+
+
+def _load_samples(lt, R, p1_per_slice):
+    """Write pass-1 entries (rows, cols, vals, col_node, g) of every slice into R.smp."""
+    smp = R.smp
+    C = R.frame.C
+    key = smp.key.cpu().numpy()
+    val = smp.val.cpu().numpy()
+    ncol = np.zeros(R.frame.S, np.int32)
+    n1 = np.zeros(R.frame.S, np.int32)
+    col_node = np.zeros(R.frame.S * C, np.int32)
+    g = np.zeros(R.frame.S * C, np.float32)
+    for s, (rows, cols, vals, cn, gg) in p1_per_slice.items():
+        o = int(smp.off_host[s])
+        key[o:o + rows.size] = ((rows.astype(np.int64) << 16) | cols).astype(np.uint32).view(np.int32)
+        val[o:o + rows.size] = vals
+        ncol[s] = cn.size
+        n1[s] = rows.size
+        col_node[s * C:s * C + cn.size] = cn
+        g[s * C:s * C + cn.size] = gg
+    smp.key.copy_(torch.from_numpy(key))
+    smp.val.copy_(torch.from_numpy(val))
+    smp.ncol.copy_(torch.from_numpy(ncol))
+    smp.n1.copy_(torch.from_numpy(n1))
+    smp.cnt.copy_(torch.from_numpy(n1))
+    smp.col_node.copy_(torch.from_numpy(col_node))
+    smp.g.copy_(torch.from_numpy(g))
+
+
+def test_pass2_draws_bit_exact(lt, tiny_gpu):
+    cfg, sc, st, R, p1, ores = tiny_gpu
+    feed = {s: (o.p1.rows, o.p1.cols, o.p1.vals.astype(np.float32), o.p1.col_node, o.p1.g.astype(np.float32))
+            for s, o in ores.items()}
+    _load_samples(lt, R, feed)
+    # the oracle draws from the same float32 g the kernel sees
+    R.pass2(cfg["frame_seed"])
+    lt.lt_sync(R.ctx)
+    for s, o in ores.items():
+        rows, cols, vals, col_node, g = R.smp.slice(s)
+        n1 = o.p1.rows.size
+        w = o.p1.g.astype(np.float32)
+        r2, c2, _, _ = o_pass2.draw_pass2(cfg["frame_seed"], s, int(st["slice_off"][s + 1] - st["slice_off"][s]),
+                                          w, o.p1.rows * o.p1.col_node.size + o.p1.cols, cfg["rate"])
+        assert np.array_equal(rows[n1:], r2) and np.array_equal(cols[n1:], c2), f"slice {s}"
+
+
+def test_eval_entries_match_oracle(lt, tiny_gpu):
+    cfg, sc, st, R, p1, ores = tiny_gpu
+    R.evaluate()
+    lt.lt_sync(R.ctx)
+    tr = st["tree"]
+    for s, o in ores.items():
+        rows, cols, vals, col_node, g = R.smp.slice(s)
+        n1 = o.p1.rows.size
+        nodes = col_node[cols[n1:]]
+        exp = shading.node_entries(st["pts_s"], sc.vpls, st["slice_off"][s] + rows[n1:], tr.rep[nodes],
+                                   o_tree.node_scale(tr, sc.vpls, nodes), sc.boxes, cfg["d_min"])
+        assert np.all(np.abs(vals[n1:] - exp) <= ENTRY_RTOL * np.abs(exp) + 1e-12), f"slice {s}"
+
+
+def test_complete_matches_oracle_als(lt, tiny_gpu):
+    """Same observed set, same init, same iterations: images within 1e-3."""
+    cfg, sc, st, R, p1, ores = tiny_gpu
+    R.complete(cfg["frame_seed"])
+    R.render_image()
+    lt.lt_sync(R.ctx)
+    img = R.img.cpu().numpy().astype(np.float64)
+    factors = []
+    for s in range(R.frame.S):
+        rows, cols, vals, col_node, g = R.smp.slice(s)
+        m_s = int(st["slice_off"][s + 1] - st["slice_off"][s])
+        U, V = o_als.complete_slice(rows, cols, vals.astype(np.float64), m_s, col_node.size, cfg["rank"],
+                                    cfg["als_iters"], cfg["lam_rel"], cfg["frame_seed"], s)
+        factors.append((U, V))
+    ref = o_render.render_slices(factors, st["row_perm"], st["slice_off"], sc.m)
+    rel = np.linalg.norm(img - ref) / np.linalg.norm(ref)
+    assert rel <= IMAGE_RTOL, rel
+
+
+def test_render_matches_factorised_sum(lt, tiny_gpu):
+    cfg, sc, st, R, p1, ores = tiny_gpu
+    r = cfg["rank"]
+    U = R.uv.U.cpu().numpy().reshape(-1, r).astype(np.float64)
+    V = R.uv.V.cpu().numpy().reshape(R.frame.S, R.frame.C, r).astype(np.float64)
+    ncol = R.smp.ncol.cpu().numpy()
+    off = st["slice_off"]
+    factors = [(U[off[s]:off[s + 1]], V[s, :ncol[s]]) for s in range(R.frame.S)]
+    ref = o_render.render_slices(factors, st["row_perm"], off, sc.m)
+    R.render_image()
+    lt.lt_sync(R.ctx)
+    img = R.img.cpu().numpy()
+    np.testing.assert_allclose(img, ref, rtol=1e-5, atol=1e-6 * ref.max())
+
+
+def test_end_to_end_frame_matches_oracle_pipeline(lt, tiny):
+    from paper_2202_12567_gb300.renderer import Renderer
+    cfg, sc, st = tiny
+    R = Renderer(sc, cfg, device=0).setup(cut=st["cut"], row_perm=st["row_perm"], slice_off=st["slice_off"])
+    img = R.render().cpu().numpy().astype(np.float64)
+    ref_img, _ = pipeline.render_frame(sc, cfg, st)
+    rel = np.linalg.norm(img - ref_img) / np.linalg.norm(ref_img)
+    assert rel <= IMAGE_RTOL, rel
+    bf = bruteforce.render(sc.points, sc.vpls, sc.boxes, cfg["d_min"])
+    print("end-to-end rel-RMSE vs brute force:", bruteforce.rel_rmse(img, bf))
+
+
+def test_empty_and_tiny_slices(lt):
+    """Slices with 0, 1 and 2 rows and a one-node cut run and give finite images."""
+    from paper_2202_12567_gb300.renderer import Renderer
+    cfg = get_config("room64_vpl1k_2box", width=8, height=8, n_vpl=16, n_slices=4, max_cut=16, rate=0.5, rank=8)
+    sc = make_scene(cfg)
+    st = pipeline.setup(sc, cfg)
+    perm = np.arange(sc.m)
+    off = np.array([0, 0, 1, 3, sc.m])
+    for cut in (st["cut"], np.array([0])):
+        R = Renderer(sc, cfg, device=0).setup(cut=cut, row_perm=perm, slice_off=off)
+        img = R.render().cpu().numpy()
+        assert np.all(np.isfinite(img))
+        assert R.smp.ncol[0].item() == 0
