@@ -2,7 +2,8 @@
 
 A step is one frame of the method's hot path (pass 1 + coarsening, pass 2, entry
 evaluation, masked-ALS completion of every slice, factorised render) on the
-256x256-point, 16384-VPL, 200-box room scene with 64 slices, 5% sampling, rank 16.
+256x256-point, 16384-VPL room scene with two boxes (the scene family of the
+learned-proposal experiments), 64 slices, 15% sampling, rank 16.
 Setup (light tree, global cut, slices) is timed separately and reported.  Quality
 is the rel-RMSE of the frame against the brute-force column sum over all VPLs
 (computed on the GPU by the library's brute-force kernel, which the tests check
@@ -29,7 +30,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "room256_vpl16k_200box"
+WORKLOAD = "room256_vpl16k_2box"
 METRIC = "ms/frame at rel-RMSE<=2% vs full-matrix render; speedup vs plain GPU form"
 
 
@@ -292,8 +293,9 @@ def run_ours(args):
     line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
                 scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
-                config=dict(workload=f"{args.workload}: 256x256 points, 16384 VPLs, 200 boxes, 64 slices, "
-                                     f"5% sampling, rank 16, 10 ALS sweeps",
+                config=dict(workload=f"{args.workload}: {sc.width}x{sc.height} points, {sc.n} VPLs, {sc.nb} boxes, "
+                                     f"{cfg['n_slices']} slices, {100 * cfg['rate']:g}% sampling, rank {cfg['rank']}, "
+                                     f"{cfg['als_iters']} ALS sweeps, cut <= {cfg['max_cut']}, tau {cfg['tau']}",
                             l2="flushed (256 MB write) between timed frames", global_cut=int(R.frame.C),
                             rel_rmse_vs_bruteforce=round(rel, 5), rays_per_pixel=round(rays_per_px, 2),
                             bruteforce_gpu_ms=round(bf_ms, 3), speedup_vs_bruteforce=round(bf_ms / ms_frame, 2),

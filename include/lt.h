@@ -173,12 +173,14 @@ lt_status lt_permute_points(lt_ctx* ctx, const float* pts, int64_t m, const int3
                             float* pts_out);
 
 /* ---- Steps 3-5 (Sec. 4, Sec. 5, Sec. 3 step 5): one frame ------------------ */
-/* Pass 1 + light coarsening (Sec. 4, Eq. 2): per slice, k_c rows per cut node drawn
- * with Philox (counter t, c, slice, 1), entries evaluated, sibling pairs merged
- * while cost = eps + cost(q) < tau * S_hat.  Writes ncol, col_node, g, the pass-1
+/* Pass 1 + light coarsening (Sec. 4, Eq. 2): per slice, k_c rows per cut node
+ * (k_c = clamp(round(max(2, rate1 m') C I_c / I_root), 2, min(64, m')), rows
+ * proportional to intensity and uniform in the slice) drawn with Philox (counter
+ * t, c, slice, 1), entries evaluated, sibling pairs merged while
+ * cost = eps + cost(q) < tau * S_hat.  Writes ncol, col_node, g, the pass-1
  * keys/values (n1 = cnt).  A slice whose entries exceed its capacity latches
  * LT_ELIMIT. */
-lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate, float tau, float d_min,
+lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, float d_min,
                           uint64_t seed, lt_samples* smp);
 /* Pass 2 (Sec. 5, Eq. 3): draws (column by the integer CDF of `weights` or of g when
  * weights is NULL, row uniform) with Philox (t, 0, slice, 2), keeping the first

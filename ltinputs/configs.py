@@ -34,19 +34,19 @@ CONFIGS = {
     # 64x64 points, 1024 VPLs, two floor boxes: the oracle renders it in seconds.
     "room64_vpl1k_2box": dict(
         _BASE, width=64, height=64, n_vpl=1024, n_big_boxes=2, n_small_boxes=0,
-        glossy_frac=0.0, n_slices=16, rate=0.10, rank=8, als_iters=10,
+        glossy_frac=0.0, n_slices=16, rate=0.10, rate1=0.03, rank=8, als_iters=10,
         max_cut=1024, scene_seed=1001,
     ),
     # 256x256 points, 16384 VPLs, 200 random boxes behind a uniform grid.
     "room256_vpl16k_200box": dict(
         _BASE, width=256, height=256, n_vpl=16384, n_big_boxes=0, n_small_boxes=200,
-        glossy_frac=0.0, n_slices=64, rate=0.05, rank=16, als_iters=10,
+        glossy_frac=0.0, n_slices=64, rate=0.05, rate1=0.015, rank=16, als_iters=10,
         max_cut=4096, scene_seed=1002,
     ),
     # 512x512 points, 65536 VPLs, 1000 boxes, Phong lobe on 30% of faces.
     "room512_vpl64k_1000box_glossy": dict(
         _BASE, width=512, height=512, n_vpl=65536, n_big_boxes=0, n_small_boxes=1000,
-        glossy_frac=0.3, n_slices=128, rate=0.05, rank=16, als_iters=10,
+        glossy_frac=0.3, n_slices=128, rate=0.05, rate1=0.015, rank=16, als_iters=10,
         max_cut=2000, scene_seed=1003,
     ),
 }
@@ -60,3 +60,12 @@ def get_config(name: str, **overrides) -> dict:
     cfg.update(overrides)
     cfg["name"] = name
     return cfg
+
+
+# 256x256 points, 16384 VPLs, the two-box generator of the tiny preset at full size:
+# the scene family the learned-proposal experiments use (held-out seeds 5000-5019).
+CONFIGS["room256_vpl16k_2box"] = dict(
+    _BASE, width=256, height=256, n_vpl=16384, n_big_boxes=2, n_small_boxes=0,
+    glossy_frac=0.0, n_slices=64, rate=0.15, rate1=0.002, rank=16, als_iters=10,
+    max_cut=16384, tau=0.0005, d_min=0.1, scene_seed=5000,
+)

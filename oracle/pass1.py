@@ -4,7 +4,7 @@ For one slice with m' rows the global cut is coarsened from sparse samples:
 
 1. Rows per cut node (Sec. 4): the number of test pixels of node c grows linearly
    with its intensity and the pixels are uniform inside the slice.  Reading:
-       kappa = max(2, 0.3 * rate * m'),   x_c = (kappa * C) * (I_c / I_root),
+       kappa = max(2, rate1 * m'),   x_c = (kappa * C) * (I_c / I_root),
        k_c   = min(max(floor(x_c + 1/2), 2), 64, m')
    in float32 (an integer decided by floating point, taken in the kernel's
    precision).  I_root is the sum of the cut intensities (the cut partitions the
@@ -76,12 +76,12 @@ def build_forest(tree: LightTree, cut) -> Forest:
     return Forest(C=C, node=node, child=child, parent=parent)
 
 
-def rows_per_node(tree: LightTree, cut, m_s: int, rate: float) -> np.ndarray:
+def rows_per_node(tree: LightTree, cut, m_s: int, rate1: float) -> np.ndarray:
     """k_c for every global-cut node (float32 decision, see module docstring)."""
     f32 = np.float32
     cut = np.asarray(cut, dtype=np.int64)
     C = cut.size
-    kappa = max(f32(2.0), f32(f32(f32(0.3) * f32(rate)) * f32(m_s)))
+    kappa = max(f32(2.0), f32(f32(rate1) * f32(m_s)))
     x = f32(kappa * f32(C)) * (tree.I[cut].astype(np.float32) / f32(tree.I[0]))
     k = np.floor((x + f32(0.5)).astype(np.float32)).astype(np.int64)
     return np.minimum(np.minimum(np.maximum(k, 2), MAX_ROWS_PER_NODE), m_s)
@@ -123,7 +123,7 @@ class Pass1Slice:
 
 
 def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int, row0: int,
-                  m_s: int, rate: float, tau: float, seed: int, d_min=0.01,
+                  m_s: int, rate1: float, tau: float, seed: int, d_min=0.01,
                   order_rng: np.random.Generator | None = None) -> Pass1Slice:
     """Pass 1 + coarsening of slice s (rows row0 .. row0+m_s-1 of the slice-ordered points)."""
     C = forest.C
@@ -144,7 +144,7 @@ def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int
                                     np.full(len(rows), rep[t]), np.full(len(rows), scale[local_node]),
                                     boxes, d_min)
 
-    k = rows_per_node(tree, forest.node[:C], m_s, rate)
+    k = rows_per_node(tree, forest.node[:C], m_s, rate1)
     rows = {}
     vals = {}
     for c in range(C):

@@ -57,7 +57,7 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
     tree, forest, pts_s = st["tree"], st["forest"], st["pts_s"]
     a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
     m_s = b - a
-    p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.boxes, s, a, m_s, cfg["rate"],
+    p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.boxes, s, a, m_s, cfg["rate1"],
                              cfg["tau"], seed, cfg["d_min"], order_rng)
     n_s = p1.col_node.size
     w = p1.g if weights is None else weights

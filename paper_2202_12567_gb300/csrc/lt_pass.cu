@@ -25,7 +25,7 @@ constexpr int kP1Threads = 512;
 constexpr int kP2Threads = 1024;
 constexpr int kMaxRowsPerNode = 64;
 constexpr int kMaxDraws = 1 << 16;
-constexpr int kMaxCut = 8192;
+constexpr int kMaxCut = 16384;
 constexpr int kStNot = 0, kStAlive = 1, kStDead = 2, kStRejected = 3;
 
 struct P1Plan {
@@ -64,7 +64,7 @@ __device__ int block_scan_array(const int32_t* in, int32_t* out, int count, int3
 }
 
 // ------------------------------------------------------------------ pass 1: plan
-__global__ void __launch_bounds__(kP1Threads) k_pass1_plan(lt_frame F, float rate, P1Plan pl) {
+__global__ void __launch_bounds__(kP1Threads) k_pass1_plan(lt_frame F, float rate1, P1Plan pl) {
     __shared__ int32_t ws[32];
     const int s = blockIdx.x;
     const int C = F.C, NF = 2 * C - 1;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_plan(lt_frame F, float rat
     int32_t* cap = pl.cap + (int64_t)s * NF;
     int32_t* off = pl.off + (int64_t)s * NF;
     int32_t* pfx = pl.pfx + (int64_t)s * (C + 1);
-    const float kappa = fmaxf(2.0f, __fmul_rn(__fmul_rn(0.3f, rate), (float)ms));
+    const float kappa = fmaxf(2.0f, __fmul_rn(rate1, (float)ms));
     const float Iroot = F.tree.I[0];
     for (int c = threadIdx.x; c < C; c += blockDim.x) {
         const int node = F.forest[8 * c];
@@ -616,9 +616,9 @@ bool samples_ok(const lt_samples* s) {
 
 }  // namespace
 
-extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate, float tau, float d_min,
+extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, float d_min,
                                      uint64_t seed, lt_samples* smp) {
-    if (!ctx || !frame_ok(f) || !samples_ok(smp) || !(rate >= 0.f) || !(tau >= 0.f))
+    if (!ctx || !frame_ok(f) || !samples_ok(smp) || !(rate1 >= 0.f) || !(tau >= 0.f))
         return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1: bad arguments");
     if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1: no scene uploaded");
     cudaSetDevice(ctx->device);
@@ -647,7 +647,7 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate,
     pl.pfx = (int32_t*)take(n_p * 4);
     if ((size_t)(p - (char*)ctx->scr[SCR_P1_PLAN]) > ctx->scr_size[SCR_P1_PLAN])
         return lt_fail(ctx, LT_ENOMEM, "lt_sample_pass1: plan layout overflow");
-    k_pass1_plan<<<S, kP1Threads, 0, ctx->stream>>>(*f, rate, pl);
+    k_pass1_plan<<<S, kP1Threads, 0, ctx->stream>>>(*f, rate1, pl);
     LT_LAUNCH_CHECK(ctx, "k_pass1_plan");
     std::vector<int64_t> tot(S), basev(S);
     LT_CUDA(ctx, cudaMemcpyAsync(tot.data(), pl.total, S * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -667,7 +667,7 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate,
     const size_t shm = (size_t)(C + 1) * sizeof(int32_t);
     if (shm > 16 * 1024)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_pass1<<<S, kP1Threads, shm, ctx->stream>>>(*f, ctx->grid, rate, tau, d_min * d_min, seed, pl, store, *smp,
+    k_pass1<<<S, kP1Threads, shm, ctx->stream>>>(*f, ctx->grid, rate1, tau, d_min * d_min, seed, pl, store, *smp,
                                                  ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_pass1");
     // memory stays referenced by the stream: the host vectors were consumed by the

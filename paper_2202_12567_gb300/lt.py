@@ -282,14 +282,14 @@ class Frame:
 class Samples:
     """Per-slice observed entries (lt_samples) with a capacity layout for ``rate``."""
 
-    def __init__(self, frame: Frame, rate: float):
+    def __init__(self, frame: Frame, rate: float, rate1: float):
         S, C = frame.S, frame.C
         dev = frame.pts_s.device
         caps = []
         for ms in frame.sizes:
-            kappa = max(2.0, 0.3 * rate * ms)
+            kappa = max(2.0, rate1 * ms)
             k_sum = min(64, ms) * C if ms else 0
-            k_sum = min(k_sum, int(kappa * C + 2.5 * C + 1))
+            k_sum = min(k_sum, int(1.001 * (kappa * C + 2.5 * C)) + 16)
             caps.append(2 * k_sum + int(math.ceil(rate * ms * C)) + 64)
         off = np.concatenate([[0], np.cumsum(caps)]).astype(np.int64)
         i32 = dict(dtype=torch.int32, device=dev)

@@ -61,7 +61,7 @@ class Renderer:
         self.row_perm, self.slice_off = row_perm, slice_off
         self.pts_s = lt.lt_permute_points(ctx, self.pts, row_perm)
         self.frame = lt.Frame(self.pts_s, self.vpls, slice_off, self.tree, cut, forest, level_off, level_nodes, H)
-        self.smp = lt.Samples(self.frame, cfg["rate"])
+        self.smp = lt.Samples(self.frame, cfg["rate"], cfg["rate1"])
         self.uv = lt.Factors(self.frame, cfg["rank"])
         self.img = torch.zeros(self.frame.m, dtype=torch.float32, device=self.dev)
         lt.lt_sync(ctx)
@@ -70,7 +70,7 @@ class Renderer:
     # ---------------------------------------------------------------- frame stages
     def pass1(self, seed):
         c = self.cfg
-        lt.lt_sample_pass1(self.ctx, self.frame, self.smp, c["rate"], c["tau"], c["d_min"], seed)
+        lt.lt_sample_pass1(self.ctx, self.frame, self.smp, c["rate1"], c["tau"], c["d_min"], seed)
 
     def pass2(self, seed, weights=None):
         lt.lt_sample_pass2(self.ctx, self.frame, self.smp, self.cfg["rate"], seed, weights)

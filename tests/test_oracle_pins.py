@@ -263,7 +263,7 @@ def tiny_setup(tiny):
 def _run_p1(cfg, sc, st, s, tau=None, order_rng=None):
     a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
     return pass1.coarsen_slice(st["tree"], st["forest"], st["pts_s"], sc.vpls, sc.boxes, s, a, b - a,
-                               cfg["rate"], cfg["tau"] if tau is None else tau, 7, cfg["d_min"],
+                               cfg["rate1"], cfg["tau"] if tau is None else tau, 7, cfg["d_min"],
                                order_rng)
 
 
@@ -314,10 +314,10 @@ def test_pass1_rows_per_node_rule(tiny_setup):
     tr = st["tree"]
     cut = st["cut"]
     m_s = 200
-    k = pass1.rows_per_node(tr, cut, m_s, cfg["rate"])
+    k = pass1.rows_per_node(tr, cut, m_s, cfg["rate1"])
     assert np.all((k >= 2) & (k <= 64))
     # proportional to intensity where the clamp is inactive (Sec. 4)
-    kappa = max(2.0, 0.3 * cfg["rate"] * m_s)
+    kappa = max(2.0, cfg["rate1"] * m_s)
     x = kappa * len(cut) * tr.I[cut].astype(np.float64) / float(tr.I[0])
     free = (x > 2.5) & (x < 63.5)
     assert np.all(np.abs(k[free] - x[free]) <= 0.5 + 1e-4)
