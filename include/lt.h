@@ -190,6 +190,19 @@ lt_status lt_sample_pass2(lt_ctx* ctx, const lt_frame* f, const float* weights, 
                           uint64_t seed, lt_samples* smp);
 /* Evaluate the entries n1[s] .. cnt[s]-1 of every slice (shadow rays inside). */
 lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min, lt_samples* smp);
+/* lt_eval_entries without any device allocation.  The paper has no counterpart:
+ * this is for callers that cannot let the library allocate device memory, such as
+ * a host application that owns the whole device-memory budget (a renderer plugin
+ * inside a frame loop), where a cudaMalloc could fail against the fixed budget or
+ * stall the device mid-frame.  Arguments, results and errors are those of
+ * lt_eval_entries; the per-slice prefix it needs lives in a fixed device array of
+ * the library (32 KB on every GPU that loads the library, held until exit), so
+ * at most 4096 slices are accepted (LT_EINVAL beyond that).  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make it
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents: calls whose work overlaps on the GPU (other streams or
+ * contexts) race on it and must be serialised by the caller. */
+lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, float d_min, lt_samples* smp);
 /* Instrumentation (no counterpart in the paper): re-runs the evaluation of the same
  * entries without storing values and returns in stats_host[4] the entries, the shadow
  * rays cast (entries with a positive unoccluded value), the grid cells visited and

@@ -13,6 +13,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "lt_internal.cuh"
@@ -701,6 +703,64 @@ extern "C" lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min
     lt_status st;
     int64_t* pfx = (int64_t*)lt_scratch(ctx, SCR_MISC, (size_t)(f->S + 1) * 8, &st);
     if (!pfx) return st;
+    k_count_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, f->S, pfx);
+    LT_LAUNCH_CHECK(ctx, "k_count_prefix");
+    const size_t shm = (size_t)(f->S + 1) * 8;
+    if (shm > 16 * 1024)
+        LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)shm));
+    k_eval_entries<false><<<ctx->num_sms * 16, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
+                                                                        nullptr);
+    LT_LAUNCH_CHECK(ctx, "k_eval_entries");
+    return LT_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free variant
+// lt_eval_entries keeps its per-slice prefix in context scratch, which it grows
+// with cudaMalloc.  Some hosts cannot allow that: an application that owns the
+// whole device-memory budget and hands the library only its inputs and outputs
+// (for example a renderer plugin running inside a frame loop), where a cudaMalloc
+// could fail against the fixed budget or stall the device in the middle of a frame.
+// For them the prefix lives in this fixed device array instead.  It is part of the
+// module image, so every GPU that loads the library holds its 32 KB until exit.
+constexpr int kNoAllocMaxSlices = 4096;
+static __device__ __align__(256) int64_t g_noalloc_prefix[kNoAllocMaxSlices + 1];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int64_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_prefix on the context's device.  In host code the
+// symbol names a host-side stand-in, so the real address is looked up once per
+// device (with that device current) and cached.
+lt_status noalloc_prefix(lt_ctx* ctx, int64_t** out) {
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+        return lt_fail(ctx, LT_EINVAL, "lt_eval_entries_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_prefix);
+        if (e != cudaSuccess) return lt_cuda_check(ctx, e, "cudaGetSymbolAddress(g_noalloc_prefix)");
+        g_noalloc_addr[ctx->device] = (int64_t*)p;
+    }
+    *out = g_noalloc_addr[ctx->device];
+    return LT_OK;
+}
+}  // namespace
+
+extern "C" lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, float d_min, lt_samples* smp) {
+    if (!ctx || !frame_ok(f) || !samples_ok(smp))
+        return lt_fail(ctx, LT_EINVAL, "lt_eval_entries_noalloc: bad arguments");
+    if (f->S > kNoAllocMaxSlices)
+        return lt_fail(ctx, LT_EINVAL,
+                       "lt_eval_entries_noalloc: at most " + std::to_string(kNoAllocMaxSlices) + " slices");
+    if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_eval_entries_noalloc: no scene uploaded");
+    LT_CUDA(ctx, cudaSetDevice(ctx->device));
+    int64_t* pfx = nullptr;
+    const lt_status st = noalloc_prefix(ctx, &pfx);
+    if (st != LT_OK) return st;
+    // every entry of the prefix that the evaluation reads is rewritten here first
     k_count_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, f->S, pfx);
     LT_LAUNCH_CHECK(ctx, "k_count_prefix");
     const size_t shm = (size_t)(f->S + 1) * 8;

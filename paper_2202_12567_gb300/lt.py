@@ -78,6 +78,7 @@ _SIGS = {
     "lt_sample_pass2": (_i32, [_p, ctypes.POINTER(lt_frame), _p, _f32, _u64, ctypes.POINTER(lt_samples)]),
     "lt_eval_entries": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples)]),
     "lt_eval_stats": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples), _p]),
+    "lt_eval_entries_noalloc": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples)]),
     "lt_complete": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _u64,
                            ctypes.POINTER(lt_factors)]),
     "lt_render": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p,
@@ -344,6 +345,12 @@ def lt_sample_pass2(ctx: Context, frame: Frame, smp: Samples, rate, seed, weight
 def lt_eval_entries(ctx: Context, frame: Frame, smp: Samples, d_min):
     ctx._check("lt_eval_entries", ctx.lib.lt_eval_entries(ctx.h, ctypes.byref(frame.struct()), d_min,
                                                           ctypes.byref(smp.struct())))
+
+
+def lt_eval_entries_noalloc(ctx: Context, frame: Frame, smp: Samples, d_min):
+    """lt_eval_entries for hosts that forbid library allocations (see include/lt.h)."""
+    ctx._check("lt_eval_entries_noalloc", ctx.lib.lt_eval_entries_noalloc(ctx.h, ctypes.byref(frame.struct()), d_min,
+                                                                          ctypes.byref(smp.struct())))
 
 
 def lt_eval_stats(ctx: Context, frame: Frame, smp: Samples, d_min) -> dict:
