@@ -33,17 +33,11 @@ struct Omega {
     float* mu;          // [S] mean observed value
     uint32_t* bm;       // row-major bitmaps
     uint32_t* bt;       // column-major bitmaps
+    uint32_t* wr;       // per word of bm: set bits before it in its row
+    uint32_t* wc;       // per word of bt: set bits before it in its column
     int64_t bm_stride, bt_stride;
     int64_t* line_pfx;  // [S + 1] prefix of n'_s (V-step lines)
 };
-
-__device__ __forceinline__ int popc_prefix(const uint32_t* words, int bit) {
-    int c = 0;
-    const int w = bit >> 5;
-    for (int i = 0; i < w; ++i) c += __popc(words[i]);
-    const uint32_t mask = (bit & 31) ? ((1u << (bit & 31)) - 1u) : 0u;
-    return c + __popc(words[w] & mask);
-}
 
 __global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omega om, int32_t* status) {
     __shared__ int32_t ws[32];
@@ -57,6 +51,8 @@ __global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omeg
     const int W = (ns + 31) >> 5, WT = (ms + 31) >> 5;
     uint32_t* bm = om.bm + (int64_t)s * om.bm_stride;
     uint32_t* bt = om.bt + (int64_t)s * om.bt_stride;
+    uint32_t* wr = om.wr + (int64_t)s * om.bm_stride;
+    uint32_t* wc = om.wc + (int64_t)s * om.bt_stride;
     const uint32_t* key = smp.key + smp.off[s];
     const float* val = smp.val + smp.off[s];
     for (int64_t i = threadIdx.x; i < (int64_t)ms * W; i += blockDim.x) bm[i] = 0u;
@@ -82,14 +78,17 @@ __global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omeg
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         om.mu[s] = ne > 0 ? t / (float)ne : 0.f;
     }
-    // row and column pointers
+    // per-word prefix counts and the row / column pointers
     int32_t* rp = om.rp + row0 + s;
     int carry = 0;
     for (int r0 = 0; r0 < ms; r0 += blockDim.x) {
         const int r = r0 + threadIdx.x;
         int c = 0;
         if (r < ms)
-            for (int w = 0; w < W; ++w) c += __popc(bm[(int64_t)r * W + w]);
+            for (int w = 0; w < W; ++w) {
+                wr[(int64_t)r * W + w] = (uint32_t)c;
+                c += __popc(bm[(int64_t)r * W + w]);
+            }
         int tot;
         const int pre = block_exclusive_scan<int>(c, ws, &tot);
         if (r < ms) rp[r] = carry + pre;
@@ -102,7 +101,10 @@ __global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omeg
         const int c = c0 + threadIdx.x;
         int n = 0;
         if (c < ns)
-            for (int w = 0; w < WT; ++w) n += __popc(bt[(int64_t)c * WT + w]);
+            for (int w = 0; w < WT; ++w) {
+                wc[(int64_t)c * WT + w] = (uint32_t)n;
+                n += __popc(bt[(int64_t)c * WT + w]);
+            }
         int tot;
         const int pre = block_exclusive_scan<int>(n, ws, &tot);
         if (c < ns) cp[c] = carry + pre;
@@ -110,13 +112,15 @@ __global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omeg
     }
     if (threadIdx.x == 0) cp[ns] = carry;
     __syncthreads();
+    // an entry's slot: pointer + bits before its word + bits before it in its word
     const int64_t o = smp.off[s];
     for (int e = threadIdx.x; e < ne; e += blockDim.x) {
         const uint32_t k = key[e];
         const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
         if (r >= ms || c >= ns) continue;
-        const int pr = rp[r] + popc_prefix(bm + (int64_t)r * W, c);
-        const int pc = cp[c] + popc_prefix(bt + (int64_t)c * WT, r);
+        const int64_t iw = (int64_t)r * W + (c >> 5), jw = (int64_t)c * WT + (r >> 5);
+        const int pr = rp[r] + (int)wr[iw] + __popc(bm[iw] & ((1u << (c & 31)) - 1u));
+        const int pc = cp[c] + (int)wc[jw] + __popc(bt[jw] & ((1u << (r & 31)) - 1u));
         om.cidx[o + pr] = (uint16_t)c;
         om.cval[o + pr] = val[e];
         om.ridx[o + pc] = (uint16_t)r;
@@ -149,37 +153,126 @@ __global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int r, uint64_t
     }
 }
 
-// Solve one line in scalar type T.  Returns false when the factorisation is not
-// acceptable in float (non-positive or badly spread pivots).
-template <int G, typename T>
-__device__ __forceinline__ bool solve_line(int len, const uint16_t* __restrict__ idx, const float* __restrict__ val,
-                                           const float* __restrict__ Fb, int r, float lam_rel, int k, T* Lsh,
-                                           T* out_k, bool check) {
+// ---- Gram matrices on the tensor cores ---------------------------------------
+// For one line (a row of U or of V) with observed entries e and gathered factor rows
+// x_e (r values each), G = sum_e x_e x_e^T = X^T X and b = sum_e a_e x_e.  X^T X is a
+// 16 x K x 16 contraction per line: mma.m16n8k8 with A = X^T (16 x 8) and B = X
+// (8 x 8) whose fragments hold the same gathered values.  Each float is split into
+// a TF32 head and a TF32 tail (x = hi + lo) and the three products hi*hi, hi*lo,
+// lo*hi are accumulated in FP32, which keeps the Gram at float32 accuracy.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float& c0, float& c1, float& c2, float& c3, uint32_t a0, uint32_t a1,
+                                         uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Whole warp: Gram and right-hand side of one line into shared memory
+// Gs[RP][RP+1] and bs[RP] (RP = 16 or 32, rows and columns >= r are zero).
+template <int RP>
+__device__ __forceinline__ void gram_tc(int len, const uint16_t* __restrict__ idx, const float* __restrict__ val,
+                                        const float* Fb, int fstride, int r, float* Gs, float* bs) {
+    constexpr int MT = RP / 16, NT = RP / 8;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float c[MT][NT][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c[i][j][q] = 0.f;
+    float bpart[MT][2];
+#pragma unroll
+    for (int i = 0; i < MT; ++i) bpart[i][0] = bpart[i][1] = 0.f;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+        const int je = e0 + lane < len ? (int)idx[e0 + lane] : -1;
+        const float ae = e0 + lane < len ? val[e0 + lane] : 0.f;
+        for (int q = 0; q < 4 && e0 + 8 * q < len; ++q) {
+            const int j0 = __shfl_sync(FULL, je, 8 * q + t), j1 = __shfl_sync(FULL, je, 8 * q + t + 4);
+            const float a0v = __shfl_sync(FULL, ae, 8 * q + t), a1v = __shfl_sync(FULL, ae, 8 * q + t + 4);
+            // x[mt][0] = X[t][16mt+g], [1] = X[t][16mt+g+8], [2] = X[t+4][16mt+g], [3] = X[t+4][16mt+g+8]
+            float x[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt) {
+                const int m0 = 16 * mt + g, m1 = m0 + 8;
+                x[mt][0] = (j0 >= 0 && m0 < r) ? Fb[j0 * fstride + m0] : 0.f;
+                x[mt][1] = (j0 >= 0 && m1 < r) ? Fb[j0 * fstride + m1] : 0.f;
+                x[mt][2] = (j1 >= 0 && m0 < r) ? Fb[j1 * fstride + m0] : 0.f;
+                x[mt][3] = (j1 >= 0 && m1 < r) ? Fb[j1 * fstride + m1] : 0.f;
+                bpart[mt][0] += a0v * x[mt][0] + a1v * x[mt][2];
+                bpart[mt][1] += a0v * x[mt][1] + a1v * x[mt][3];
+            }
+            uint32_t hi[MT][4], lo[MT][4];
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) split_tf32(x[mt][i], hi[mt][i], lo[mt][i]);
+            // B of column tile nt (columns 8nt .. 8nt+7): (X[t][8nt+g], X[t+4][8nt+g])
+#pragma unroll
+            for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    const int bm = nt >> 1, bo = nt & 1;  // rows 8nt+g live in x[bm][bo], x[bm][bo+2]
+                    float* cc = c[mt][nt];
+                    mma_tf32(cc[0], cc[1], cc[2], cc[3], hi[mt][0], hi[mt][1], hi[mt][2], hi[mt][3], hi[bm][bo],
+                             hi[bm][bo + 2]);
+                    mma_tf32(cc[0], cc[1], cc[2], cc[3], hi[mt][0], hi[mt][1], hi[mt][2], hi[mt][3], lo[bm][bo],
+                             lo[bm][bo + 2]);
+                    mma_tf32(cc[0], cc[1], cc[2], cc[3], lo[mt][0], lo[mt][1], lo[mt][2], lo[mt][3], hi[bm][bo],
+                             hi[bm][bo + 2]);
+                }
+        }
+    }
+    // C fragment: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1) of each 16 x 8 tile
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const int row = 16 * mt + g, col = 8 * nt + 2 * t;
+            Gs[row * (RP + 1) + col] = c[mt][nt][0];
+            Gs[row * (RP + 1) + col + 1] = c[mt][nt][1];
+            Gs[(row + 8) * (RP + 1) + col] = c[mt][nt][2];
+            Gs[(row + 8) * (RP + 1) + col + 1] = c[mt][nt][3];
+        }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v = bpart[mt][h];
+            v += __shfl_xor_sync(FULL, v, 1);
+            v += __shfl_xor_sync(FULL, v, 2);
+            if (t == 0) bs[16 * mt + 8 * h + g] = v;
+        }
+}
+
+// A group of G lanes solves (Gram + ridge) u = b for one line: lane k loads row k of
+// the Gram Gs (row stride G + 1) and b_k into registers.  Returns false when the
+// float factorisation is not acceptable (a non-positive pivot, or pivots spread by
+// more than 1/kPivotRatio).
+template <int G, typename T, bool SMEM_L>
+__device__ __forceinline__ bool factor_solve(const float* Gs, const float* bs, bool live, int len, int r,
+                                             float lam_rel, int k, T* out_k, bool check, float* Lsh) {
     const unsigned FULL = 0xffffffffu;
     T acc[G];
 #pragma unroll
-    for (int c = 0; c < G; ++c) acc[c] = T(0);
-    T rhs = T(0);
-    // warp-uniform trip count: every group of the warp runs max(len) steps
-    int lmax = len;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lmax = max(lmax, __shfl_xor_sync(FULL, lmax, o));
-    for (int e = 0; e < lmax; ++e) {
-        T fk = T(0), a = T(0);
-        if (e < len) {
-            const int j = idx[e];
-            a = (T)val[e];
-            if (k < r) fk = (T)__ldg(Fb + (int64_t)j * r + k);
-        }
-#pragma unroll
-        for (int c = 0; c < G; ++c) {
-            const T fc = __shfl_sync(FULL, fk, c, G);
-            acc[c] += fk * fc;
-        }
-        rhs += a * fk;
-    }
-    // trace and ridge
-    T tr = acc[0] * T(0);
+    for (int c = 0; c < G; ++c) acc[c] = live ? (T)Gs[k * (G + 1) + c] : T(0);
+    T rhs = live ? (T)bs[k] : T(0);
+    if (!live) len = 0;
+    T tr = T(0);
 #pragma unroll
     for (int c = 0; c < G; ++c)
         if (c == k) tr = acc[c];
@@ -207,8 +300,10 @@ __device__ __forceinline__ bool solve_line(int len, const uint16_t* __restrict__
             dmin = djj < dmin ? djj : dmin;
             dmax = djj > dmax ? djj : dmax;
         }
-        const T ljj = sqrt(djj > T(0) ? djj : T(1));
-        const T lij = (k > j) ? acc[j] / ljj : (k == j ? ljj : T(0));
+        const T dpos = djj > T(0) ? djj : T(1);
+        const T ljj = sqrt(dpos);
+        const T inv = T(1) / ljj;
+        const T lij = (k > j) ? acc[j] * inv : (k == j ? ljj : T(0));
         acc[j] = lij;
 #pragma unroll
         for (int c = j + 1; c < G; ++c) {
@@ -217,107 +312,335 @@ __device__ __forceinline__ bool solve_line(int len, const uint16_t* __restrict__
         }
     }
     if (check && !zero && (!ok || dmin < (T)kPivotRatio * dmax)) return false;
-    // triangular solves through shared memory (row k of L)
+    if (SMEM_L) {
+        // triangular solves through shared memory (Lsh may alias this line's Gram:
+        // every lane has read its row before any lane writes here)
+        __syncwarp();
+        // row k of L; the diagonal slot holds 1 / L[k][k]
+        T dk = T(1);
 #pragma unroll
-    for (int c = 0; c < G; ++c) Lsh[k * G + c] = acc[c];
-    __syncwarp();
-    // forward: L y = b (lane k holds b_k)
+        for (int c = 0; c < G; ++c)
+            if (c == k) dk = acc[c];
+#pragma unroll
+        for (int c = 0; c < G; ++c) Lsh[k * G + c] = (c == k) ? (float)(T(1) / dk) : (float)acc[c];
+        __syncwarp();
+        T y = rhs;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const T yj = __shfl_sync(FULL, y, j, G) * (T)Lsh[j * G + j];
+            if (k == j) y = yj;
+            else if (k > j) y -= (T)Lsh[k * G + j] * yj;
+        }
+        T x = y;
+#pragma unroll
+        for (int j = G - 1; j >= 0; --j) {
+            const T xj = __shfl_sync(FULL, x, j, G) * (T)Lsh[j * G + j];
+            if (k == j) x = xj;
+            else if (k < j) x -= (T)Lsh[j * G + k] * xj;
+        }
+        __syncwarp();
+        *out_k = (zero || k >= r) ? T(0) : x;
+        return true;
+    }
+    if (SMEM_L) return true;  // not reached
+    // forward L y = b: lane k holds L[k][0..k] in acc[0..k]
     T y = rhs;
+#pragma unroll
     for (int j = 0; j < G; ++j) {
-        const T yj = __shfl_sync(FULL, y, j, G) / Lsh[j * G + j];
+        const T yj = __shfl_sync(FULL, y, j, G) / __shfl_sync(FULL, acc[j], j, G);
         if (k == j) y = yj;
-        else if (k > j) y -= Lsh[k * G + j] * yj;
+        else if (k > j) y -= acc[j] * yj;
     }
-    // backward: L^T x = y
+    // backward L^T x = y: x_j is final at step j; L[j][c] (c < j) comes from lane j
     T x = y;
+#pragma unroll
     for (int j = G - 1; j >= 0; --j) {
-        const T xj = __shfl_sync(FULL, x, j, G) / Lsh[j * G + j];
+        const T xj = __shfl_sync(FULL, x, j, G) / __shfl_sync(FULL, acc[j], j, G);
         if (k == j) x = xj;
-        else if (k < j) x -= Lsh[j * G + k] * xj;
+#pragma unroll
+        for (int c = 0; c < j; ++c) {
+            const T ljc = __shfl_sync(FULL, acc[c], j, G);
+            if (k == c) x -= ljc * xj;
+        }
     }
-    __syncwarp();
     *out_k = (zero || k >= r) ? T(0) : x;
     return true;
 }
 
-// One half-step: lines are slice rows (U-step, rows_side = true) or slice columns.
-template <int G>
-constexpr int als_warps() { return G == 32 ? 4 : 8; }
+// One half-step: rows of U (rows_side) or columns of V, slice by slice.  CTA
+// (p, s) takes the p-th of P equal parts of the lines of slice s.  The other side's
+// factor of the slice (V_s for the U-step, U_s for the V-step) is staged in shared
+// memory with row stride RP + 1 when it fits, so that the gathers of the Gram are
+// shared-memory loads; a warp builds the Grams of its lines on the tensor cores and
+// groups of RP lanes factor and solve them.
+template <int RP>
+__host__ __device__ constexpr int als_warps() { return RP == 32 ? 8 : 16; }
 
-template <int G>
-__global__ void __launch_bounds__(32 * als_warps<G>()) k_als_half(lt_frame F, lt_samples smp, Omega om, int r,
-                                                                  float lam_rel, bool rows_side,
-                                                                  const float* __restrict__ Fin,
-                                                                  float* __restrict__ Fout, int32_t* n_fp64) {
-    __shared__ double Lsh_all[als_warps<G>()][32 / G][G * G];
-    __shared__ int64_t spfx[1025];
-    const int S = F.S;
+template <int RP>
+__global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F, lt_samples smp, Omega om, int r,
+                                                                   float lam_rel, bool rows_side,
+                                                                   const float* __restrict__ Fin,
+                                                                   float* __restrict__ Fout, int32_t* n_fp64,
+                                                                   int stage_rows) {
+    constexpr int LPW = 32 / RP;  // lines per warp
+    constexpr int NW = als_warps<RP>();
+    extern __shared__ float stage[];                       // [stage_rows][RP + 1]
+    __shared__ float Gs_all[NW][LPW][RP * (RP + 1)];
+    __shared__ float bs_all[NW][LPW][RP];
+    const int s = blockIdx.y, P = gridDim.x, p = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int grp = lane / G, k = lane % G;
-    const int gpw = 32 / G;
-    int64_t nlines;
-    if (rows_side) {
-        for (int i = threadIdx.x; i <= S; i += blockDim.x) spfx[i] = F.slice_off[i];
-        nlines = F.m;
-    } else {
-        for (int i = threadIdx.x; i <= S; i += blockDim.x) spfx[i] = om.line_pfx[i];
-        __syncthreads();
-        nlines = spfx[S];
+    const int grp = lane / RP, k = lane % RP;
+    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
+    const int ns = smp.ncol[s];
+    const int nlines = rows_side ? ms : ns;
+    const int l0 = (int)((int64_t)nlines * p / P), l1 = (int)((int64_t)nlines * (p + 1) / P);
+    if (l0 >= l1) return;
+    const float* src = rows_side ? Fin + (int64_t)s * F.C * r : Fin + (int64_t)row0 * r;
+    const int nsrc = rows_side ? ns : ms;
+    const bool staged = nsrc <= stage_rows;
+    if (staged) {
+        for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
+            const int row = i / RP, c = i % RP;
+            stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * r + c) : 0.f;
+        }
     }
     __syncthreads();
-    const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t wglobal = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-    for (int64_t base = wglobal * gpw; base < nlines; base += warps_total * gpw) {
-        const int64_t line = base + grp;
-        const bool live = line < nlines;
-        int s = 0, len = 0;
-        const uint16_t* idx = nullptr;
-        const float* vv = nullptr;
-        const float* Fb = Fin;
-        float* dst = nullptr;
-        if (live) {
-            int lo = 0, hi = S;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (spfx[mid] <= line) lo = mid;
-                else hi = mid;
-            }
-            s = lo;
-            const int64_t o = smp.off[s];
+    const float* Fb = staged ? stage : src;
+    const int fstride = staged ? RP + 1 : r;
+    const int64_t o = smp.off[s];
+    for (int base = l0 + wid * LPW; base < l1; base += NW * LPW) {
+        int my_len = 0;
+        float* my_dst = nullptr;
+#pragma unroll
+        for (int q = 0; q < LPW; ++q) {
+            const int line = base + q;
+            if (line >= l1) break;  // warp-uniform
+            int len;
+            const uint16_t* idx;
+            const float* vv;
+            float* dst;
             if (rows_side) {
-                const int rloc = (int)(line - F.slice_off[s]);
-                const int32_t* rp = om.rp + F.slice_off[s] + s;
-                const int b = rp[rloc];
-                len = rp[rloc + 1] - b;
+                const int32_t* rp = om.rp + row0 + s;
+                const int b = rp[line];
+                len = rp[line + 1] - b;
                 idx = om.cidx + o + b;
                 vv = om.cval + o + b;
-                Fb = Fin + (int64_t)s * F.C * r;                 // V of the slice
-                dst = Fout + line * r;                            // U row
+                dst = Fout + (int64_t)(row0 + line) * r;           // U row
             } else {
-                const int c = (int)(line - spfx[s]);
                 const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
-                const int b = cp[c];
-                len = cp[c + 1] - b;
+                const int b = cp[line];
+                len = cp[line + 1] - b;
                 idx = om.ridx + o + b;
                 vv = om.rval + o + b;
-                Fb = Fin + (int64_t)F.slice_off[s] * r;          // U rows of the slice
-                dst = Fout + ((int64_t)s * F.C + c) * r;          // V row
+                dst = Fout + ((int64_t)s * F.C + line) * r;        // V row
+            }
+            gram_tc<RP>(len, idx, vv, Fb, fstride, r, &Gs_all[wid][q][0], &bs_all[wid][q][0]);
+            if (grp == q) {
+                my_len = len;
+                my_dst = dst;
             }
         }
-        float* Lf = reinterpret_cast<float*>(&Lsh_all[wid][grp][0]);
+        __syncwarp();
+        const bool live = base + grp < l1;
+        const float* Gs = &Gs_all[wid][grp][0];
+        const float* bs = &bs_all[wid][grp][0];
         float xf;
-        const bool okf = solve_line<G, float>(len, idx, vv, Fb, r, lam_rel, k, Lf, &xf, true);
+        const bool okf = factor_solve<RP, float, true>(Gs, bs, live, my_len, r, lam_rel, k, &xf, true,
+                                                 &Gs_all[wid][grp][0]);
         const unsigned bad = __ballot_sync(0xffffffffu, live && !okf);
-        if (bad) {
+        if (bad) {  // float64 retry of the lines whose float pivots were not acceptable
             double xd;
-            solve_line<G, double>(len, idx, vv, Fb, r, lam_rel, k, &Lsh_all[wid][grp][0], &xd, false);
+            factor_solve<RP, double, false>(Gs, bs, live, my_len, r, lam_rel, k, &xd, false, nullptr);
             if (live && !okf) {
                 xf = (float)xd;
                 if (k == 0) atomicAdd(n_fp64, 1);
             }
         }
-        if (live && k < r) dst[k] = xf;
+        if (live && k < r) my_dst[k] = xf;
+        __syncwarp();
     }
+}
+
+// ---- rank <= 16: Gram on the tensor cores, then one thread per line ------------
+// The in-warp Cholesky of the line solve costs as many warp instructions as the
+// whole tensor-core Gram; a 16 x 16 Cholesky fits one thread's registers instead.
+// k_gram16 writes the lower triangle of every line's Gram and its right-hand side
+// element-major (Gg[e * stride + line], 136 + 16 values per line) into a buffer that
+// stays in L2; k_solve16 gives each line to one thread.
+constexpr int kGramVals = 136 + 16;
+
+__global__ void __launch_bounds__(512, 1) k_gram16(lt_frame F, lt_samples smp, Omega om, int r, bool rows_side,
+                                                   const float* __restrict__ Fin, float* __restrict__ Gg,
+                                                   int64_t stride, int stage_rows) {
+    constexpr int RP = 16, NW = 16;
+    extern __shared__ float stage[];                   // [stage_rows][RP + 1]
+    __shared__ float Gs_all[NW][RP * (RP + 1)];
+    __shared__ float bs_all[NW][RP];
+    const int s = blockIdx.y, P = gridDim.x, p = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
+    const int ns = smp.ncol[s];
+    const int nlines = rows_side ? ms : ns;
+    const int l0 = (int)((int64_t)nlines * p / P), l1 = (int)((int64_t)nlines * (p + 1) / P);
+    if (l0 >= l1) return;
+    const float* src = rows_side ? Fin + (int64_t)s * F.C * r : Fin + (int64_t)row0 * r;
+    const int nsrc = rows_side ? ns : ms;
+    const bool staged = nsrc <= stage_rows;
+    if (staged) {
+        for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
+            const int row = i / RP, c = i % RP;
+            stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * r + c) : 0.f;
+        }
+    }
+    __syncthreads();
+    const float* Fb = staged ? stage : src;
+    const int fstride = staged ? RP + 1 : r;
+    const int64_t o = smp.off[s];
+    const int64_t gbase = rows_side ? (int64_t)row0 : om.line_pfx[s];
+    float* Gs = &Gs_all[wid][0];
+    float* bs = &bs_all[wid][0];
+    for (int line = l0 + wid; line < l1; line += NW) {
+        int len;
+        const uint16_t* idx;
+        const float* vv;
+        if (rows_side) {
+            const int32_t* rp = om.rp + row0 + s;
+            const int b = rp[line];
+            len = rp[line + 1] - b;
+            idx = om.cidx + o + b;
+            vv = om.cval + o + b;
+        } else {
+            const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
+            const int b = cp[line];
+            len = cp[line + 1] - b;
+            idx = om.ridx + o + b;
+            vv = om.rval + o + b;
+        }
+        gram_tc<RP>(len, idx, vv, Fb, fstride, r, Gs, bs);
+        __syncwarp();
+        const int64_t gl = gbase + line;
+        for (int q = lane; q < RP * RP; q += 32) {
+            const int i = q / RP, j = q % RP;
+            if (j <= i) Gg[(int64_t)(i * (i + 1) / 2 + j) * stride + gl] = Gs[i * (RP + 1) + j];
+        }
+        if (lane < RP) Gg[(int64_t)(136 + lane) * stride + gl] = bs[lane];
+        __syncwarp();
+    }
+}
+
+// Solve (G + lambda I) u = b for one line per thread.  T = float with a pivot check,
+// or T = double for the retry of the lines that fail it.
+template <typename T>
+__device__ __forceinline__ bool solve16(const float* __restrict__ Gg, int64_t stride, int64_t gl, int r,
+                                        float lam_rel, bool check, T* u) {
+    T a[136], b[16];
+#pragma unroll
+    for (int e = 0; e < 136; ++e) a[e] = (T)__ldg(Gg + (int64_t)e * stride + gl);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) b[i] = (T)__ldg(Gg + (int64_t)(136 + i) * stride + gl);
+    T tr = T(0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) tr += a[i * (i + 1) / 2 + i];
+    if (!(tr > T(0))) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) u[i] = T(0);
+        return true;
+    }
+    const T lam = (T)lam_rel * tr / (T)r;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        if (i < r) {
+            a[i * (i + 1) / 2 + i] += lam;
+        } else {  // padding: identity rows, zero right-hand side
+#pragma unroll
+            for (int j = 0; j <= i; ++j) a[i * (i + 1) / 2 + j] = (j == i) ? T(1) : T(0);
+            b[i] = T(0);
+        }
+    }
+    // Cholesky (Crout order), L overwrites the lower triangle
+    T dmin = T(3.0e38), dmax = T(0);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        T d = a[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= a[j * (j + 1) / 2 + k] * a[j * (j + 1) / 2 + k];
+        if (j < r) {
+            ok &= d > T(0);
+            dmin = d < dmin ? d : dmin;
+            dmax = d > dmax ? d : dmax;
+        }
+        const T ljj = sqrt(d > T(0) ? d : T(1));
+        const T inv = T(1) / ljj;
+        a[j * (j + 1) / 2 + j] = ljj;
+#pragma unroll
+        for (int i = j + 1; i < 16; ++i) {
+            T t = a[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= a[i * (i + 1) / 2 + k] * a[j * (j + 1) / 2 + k];
+            a[i * (i + 1) / 2 + j] = t * inv;
+        }
+    }
+    if (check && (!ok || dmin < (T)kPivotRatio * dmax)) return false;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {  // L y = b
+        T t = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) t -= a[i * (i + 1) / 2 + k] * b[k];
+        b[i] = t / a[i * (i + 1) / 2 + i];
+    }
+#pragma unroll
+    for (int i = 15; i >= 0; --i) {  // L^T x = y
+        T t = b[i];
+#pragma unroll
+        for (int k = i + 1; k < 16; ++k) t -= a[k * (k + 1) / 2 + i] * b[k];
+        b[i] = t / a[i * (i + 1) / 2 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) u[i] = i < r ? b[i] : T(0);
+    return true;
+}
+
+__device__ __forceinline__ int64_t solve_line_out(const lt_frame& F, const Omega& om, bool rows_side, int64_t t) {
+    if (rows_side) return t;
+    int lo = 0, hi = F.S;  // slice of compact column t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (om.line_pfx[mid] <= t) lo = mid;
+        else hi = mid;
+    }
+    return (int64_t)lo * F.C + (t - om.line_pfx[lo]);
+}
+
+__global__ void __launch_bounds__(128) k_solve16(lt_frame F, Omega om, const float* __restrict__ Gg, int64_t stride,
+                                                 int r, float lam_rel, bool rows_side, float* __restrict__ Fout,
+                                                 uint8_t* __restrict__ retry) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nl = rows_side ? F.m : om.line_pfx[F.S];
+    if (t >= nl) return;
+    float u[16];
+    const bool ok = solve16<float>(Gg, stride, t, r, lam_rel, true, u);
+    retry[t] = ok ? 0 : 1;
+    if (!ok) return;
+    float* dst = Fout + solve_line_out(F, om, rows_side, t) * r;
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        if (i < r) dst[i] = u[i];
+}
+
+// float64 retry of the lines whose float pivots were not acceptable
+__global__ void __launch_bounds__(64) k_solve16_retry(lt_frame F, Omega om, const float* __restrict__ Gg,
+                                                      int64_t stride, int r, float lam_rel, bool rows_side,
+                                                      float* __restrict__ Fout, const uint8_t* __restrict__ retry,
+                                                      int32_t* n_fp64) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nl = rows_side ? F.m : om.line_pfx[F.S];
+    if (t >= nl || !retry[t]) return;
+    double u[16];
+    solve16<double>(Gg, stride, t, r, lam_rel, false, u);
+    float* dst = Fout + solve_line_out(F, om, rows_side, t) * r;
+    for (int i = 0; i < r && i < 16; ++i) dst[i] = (float)u[i];
+    atomicAdd(n_fp64, 1);
 }
 
 __global__ void k_render(lt_frame F, lt_samples smp, const float* __restrict__ U, const float* __restrict__ V,
@@ -376,7 +699,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     lt_status st;
     char* p = (char*)lt_scratch(ctx, SCR_OMEGA,
                                 (size_t)(f->m + S) * 4 + (size_t)S * (C + 1) * 4 + (size_t)E * 12 + S * 8 +
-                                    (size_t)S * (om.bm_stride + om.bt_stride) * 4 + (S + 1) * 8 + 16 * 256,
+                                    (size_t)S * (om.bm_stride + om.bt_stride) * 8 + (S + 1) * 8 + 16 * 256,
                                 &st);
     if (!p) return st;
     auto take = [&](size_t nbytes) {
@@ -393,6 +716,8 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.mu = (float*)take(S * 4);
     om.bm = (uint32_t*)take((size_t)S * om.bm_stride * 4);
     om.bt = (uint32_t*)take((size_t)S * om.bt_stride * 4);
+    om.wr = (uint32_t*)take((size_t)S * om.bm_stride * 4);
+    om.wc = (uint32_t*)take((size_t)S * om.bt_stride * 4);
     om.line_pfx = (int64_t*)take((S + 1) * 8);
     int32_t* n64 = (int32_t*)lt_scratch(ctx, SCR_ALS, 256, &st);
     if (!n64) return st;
@@ -404,21 +729,52 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const int r = uv->r;
     k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, r, seed, uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
-    const int blocks = ctx->num_sms * 4;
+    // CTAs per slice: about two per SM over the whole grid
+    const int P = std::max(1, (2 * ctx->num_sms + S - 1) / S);
+    const int RP = r <= 16 ? 16 : 32;
+    // static shared memory of the kernel per CTA, the rest of 200 KB stages factor rows
+    const size_t stat = (size_t)(RP == 32 ? 8 : 16) * (32 / RP) * (RP * (RP + 1) + RP) * 4;
+    const size_t budget = (size_t)210 * 1024 > stat ? (size_t)210 * 1024 - stat : 0;
+    const int stage_rows = (int)std::min<size_t>(budget / ((RP + 1) * 4), (size_t)1 << 20);
+    const size_t dyn = (size_t)stage_rows * (RP + 1) * 4;
+    if (RP == 32)
+        LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    if (RP == 16) {
+        // Gram buffer: element-major, one column per line (rows or compact columns)
+        const int64_t stride = std::max<int64_t>(f->m, (int64_t)S * C);
+        char* gp = (char*)lt_scratch(ctx, SCR_GRAM, (size_t)kGramVals * stride * 4 + stride + 256, &st);
+        if (!gp) return st;
+        float* Gg = (float*)gp;
+        uint8_t* retry = (uint8_t*)(gp + (size_t)kGramVals * stride * 4);
+        const size_t gstat = (size_t)16 * (17 * 16 + 16) * 4;
+        const int grows = (int)(((size_t)210 * 1024 - gstat) / (17 * 4));
+        const size_t gdyn = (size_t)grows * 17 * 4;
+        LT_CUDA(ctx, cudaFuncSetAttribute(k_gram16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gdyn));
+        for (int it = 0; it < iters; ++it) {
+            for (int side = 0; side < 2; ++side) {
+                const bool rows = side == 0;
+                const float* fin = rows ? uv->V : uv->U;
+                float* fout = rows ? uv->U : uv->V;
+                k_gram16<<<dim3(P, S), 512, gdyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, Gg, stride, grows);
+                LT_LAUNCH_CHECK(ctx, "k_gram16");
+                const int64_t nl = rows ? f->m : (int64_t)S * C;
+                k_solve16<<<(unsigned)((nl + 127) / 128), 128, 0, ctx->stream>>>(*f, om, Gg, stride, r, lam_rel, rows,
+                                                                                  fout, retry);
+                LT_LAUNCH_CHECK(ctx, "k_solve16");
+                k_solve16_retry<<<(unsigned)((nl + 63) / 64), 64, 0, ctx->stream>>>(*f, om, Gg, stride, r, lam_rel,
+                                                                                    rows, fout, retry, n64);
+                LT_LAUNCH_CHECK(ctx, "k_solve16_retry");
+            }
+        }
+        return LT_OK;
+    }
     for (int it = 0; it < iters; ++it) {
         for (int side = 0; side < 2; ++side) {
             const bool rows = side == 0;
             const float* fin = rows ? uv->V : uv->U;
             float* fout = rows ? uv->U : uv->V;
-            if (r <= 8)
-                k_als_half<8><<<blocks, 32 * als_warps<8>(), 0, ctx->stream>>>(*f, *smp, om, r, lam_rel, rows, fin,
-                                                                                fout, n64);
-            else if (r <= 16)
-                k_als_half<16><<<blocks, 32 * als_warps<16>(), 0, ctx->stream>>>(*f, *smp, om, r, lam_rel, rows, fin,
-                                                                                  fout, n64);
-            else
-                k_als_half<32><<<2 * blocks, 32 * als_warps<32>(), 0, ctx->stream>>>(*f, *smp, om, r, lam_rel, rows,
-                                                                                      fin, fout, n64);
+            k_als_half<32><<<dim3(P, S), 32 * als_warps<32>(), dyn, ctx->stream>>>(*f, *smp, om, r, lam_rel, rows,
+                                                                                    fin, fout, n64, stage_rows);
             LT_LAUNCH_CHECK(ctx, "k_als_half");
         }
     }

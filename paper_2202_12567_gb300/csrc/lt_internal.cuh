@@ -313,6 +313,7 @@ enum ScratchSlot {
     SCR_MISC,           // small reductions
     SCR_SORT,           // sort keys
     SCR_CUT,            // global-cut work arrays
+    SCR_GRAM,           // per-line Gram matrices of an ALS half-step
     SCR_NSLOTS
 };
 

@@ -24,6 +24,7 @@ using namespace ltk;
 namespace {
 
 constexpr int kP1Threads = 512;
+constexpr int kPairLanes = 8;   // lanes per sibling-pair test
 constexpr int kP2Threads = 1024;
 constexpr int kMaxRowsPerNode = 64;
 constexpr int kMaxDraws = 1 << 16;
@@ -206,107 +207,115 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1(lt_frame F, Grid g, float 
     __syncthreads();
     const float thr = s_thr;
 
-    // -- C: coarsening, one forest level per round, one warp per sibling pair
-    for (int h = 1; h <= F.H; ++h) {
-        const int l0 = F.level_off[h], l1 = F.level_off[h + 1];
-        for (int li = l0 + wid; li < l1; li += nw) {
-            const int f = F.level_nodes[li];
-            const int* fx = F.forest + 8 * f;
-            const int a = fx[1], b = fx[2];
-            if (state[a] != kStAlive || state[b] != kStAlive) continue;
-            const int ta = F.forest[8 * a], tb = F.forest[8 * b], tf = fx[0];
-            const float Ia = F.tree.I[ta], Ib = F.tree.I[tb], If = F.tree.I[tf];
-            const bool p_is_a = Ia >= Ib;
-            const int na = cnt[a], nb = cnt[b];
-            const int32_t* ra = rows + off[a];
-            const int32_t* rb = rows + off[b];
-            const float* va = v0 + off[a];
-            const float* vb = v0 + off[b];
-            int32_t* rf = rows + off[f];
-            float* fa = v0 + off[f];
-            float* fb = v1 + off[f];
-            const float sa = node_scale(F.tree, vpls, F.n, ta), sb = node_scale(F.tree, vpls, F.n, tb);
-            const PointRec La = load_rec(vpls, F.n, F.tree.rep[ta]);
-            const PointRec Lb = load_rec(vpls, F.n, F.tree.rep[tb]);
-            // Union of two sorted row sets: the slot of a row is the number of distinct
-            // rows below it, i.e. (rows of a below) + (rows of b below) - (rows in both
-            // below); the last term is a running ballot count over each list.
-            const unsigned lt_mask = (1u << lane) - 1u;
-            int common = 0;
-            for (int i0 = 0; i0 < na; i0 += 32) {
-                const int i = i0 + lane;
-                int x = 0, pb = 0;
-                bool both = false;
-                if (i < na) {
-                    x = ra[i];
-                    pb = lower_bound<int32_t>(rb, nb, x);
-                    both = pb < nb && rb[pb] == x;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, both);
-                if (i < na) {
-                    const int slot = i + pb - (common + __popc(bal & lt_mask));
-                    float xb;
-                    if (both) {
-                        xb = vb[pb];
-                    } else {
-                        const PointRec P = load_rec(pts, F.m, row0 + x);
-                        xb = entry_value(P, Lb, sb, dmin2, g);
+    // -- C: coarsening, one forest level per round, one group of kPairLanes lanes per
+    //       sibling pair (most pairs union only a few rows)
+    {
+        constexpr int GS = kPairLanes;
+        const int grp = lane / GS, gl = lane % GS;
+        const unsigned gmask = ((GS == 32) ? 0xffffffffu : ((1u << GS) - 1u)) << (grp * GS);
+        const unsigned lt_mask = (1u << gl) - 1u;
+        const int ngroups = nw * (32 / GS), gid = wid * (32 / GS) + grp;
+        for (int h = 1; h <= F.H; ++h) {
+            const int l0 = F.level_off[h], l1 = F.level_off[h + 1];
+            for (int li = l0 + gid; li < l1; li += ngroups) {
+                const int f = F.level_nodes[li];
+                const int* fx = F.forest + 8 * f;
+                const int a = fx[1], b = fx[2];
+                if (state[a] != kStAlive || state[b] != kStAlive) continue;  // uniform in the group
+                const int ta = F.forest[8 * a], tb = F.forest[8 * b], tf = fx[0];
+                const float Ia = F.tree.I[ta], Ib = F.tree.I[tb], If = F.tree.I[tf];
+                const bool p_is_a = Ia >= Ib;
+                const int na = cnt[a], nb = cnt[b];
+                const int32_t* ra = rows + off[a];
+                const int32_t* rb = rows + off[b];
+                const float* va = v0 + off[a];
+                const float* vb = v0 + off[b];
+                int32_t* rf = rows + off[f];
+                float* fa = v0 + off[f];
+                float* fb = v1 + off[f];
+                const float sa = node_scale(F.tree, vpls, F.n, ta), sb = node_scale(F.tree, vpls, F.n, tb);
+                const PointRec La = load_rec(vpls, F.n, F.tree.rep[ta]);
+                const PointRec Lb = load_rec(vpls, F.n, F.tree.rep[tb]);
+                // Union of two sorted row sets: the slot of a row is the number of
+                // distinct rows below it, i.e. (rows of a below) + (rows of b below) -
+                // (rows in both below); the last term is a running ballot count.
+                int common = 0;
+                for (int i0 = 0; i0 < na; i0 += GS) {
+                    const int i = i0 + gl;
+                    int x = 0, pb = 0;
+                    bool both = false;
+                    if (i < na) {
+                        x = ra[i];
+                        pb = lower_bound<int32_t>(rb, nb, x);
+                        both = pb < nb && rb[pb] == x;
                     }
-                    rf[slot] = x;
-                    fa[slot] = va[i];
-                    fb[slot] = xb;
+                    const unsigned bal = (__ballot_sync(gmask, both) >> (grp * GS)) & (gmask >> (grp * GS));
+                    if (i < na) {
+                        const int slot = i + pb - (common + __popc(bal & lt_mask));
+                        float xb;
+                        if (both) {
+                            xb = vb[pb];
+                        } else {
+                            const PointRec P = load_rec(pts, F.m, row0 + x);
+                            xb = entry_value(P, Lb, sb, dmin2, g);
+                        }
+                        rf[slot] = x;
+                        fa[slot] = va[i];
+                        fb[slot] = xb;
+                    }
+                    common += __popc(bal);
                 }
-                common += __popc(bal);
-            }
-            int seen = 0;  // rows of b (so far) that are also in a
-            for (int j0 = 0; j0 < nb; j0 += 32) {
-                const int j = j0 + lane;
-                int y = 0, pa = 0;
-                bool both = false;
-                if (j < nb) {
-                    y = rb[j];
-                    pa = lower_bound<int32_t>(ra, na, y);
-                    both = pa < na && ra[pa] == y;
+                int seen = 0;  // rows of b (so far) that are also in a
+                for (int j0 = 0; j0 < nb; j0 += GS) {
+                    const int j = j0 + gl;
+                    int y = 0, pa = 0;
+                    bool both = false;
+                    if (j < nb) {
+                        y = rb[j];
+                        pa = lower_bound<int32_t>(ra, na, y);
+                        both = pa < na && ra[pa] == y;
+                    }
+                    const unsigned bal = (__ballot_sync(gmask, both) >> (grp * GS)) & (gmask >> (grp * GS));
+                    if (j < nb && !both) {
+                        const int slot = j + pa - (seen + __popc(bal & lt_mask));
+                        const PointRec P = load_rec(pts, F.m, row0 + y);
+                        rf[slot] = y;
+                        fa[slot] = entry_value(P, La, sa, dmin2, g);
+                        fb[slot] = vb[j];
+                    }
+                    seen += __popc(bal);
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, both);
-                if (j < nb && !both) {
-                    const int slot = j + pa - (seen + __popc(bal & lt_mask));
-                    const PointRec P = load_rec(pts, F.m, row0 + y);
-                    rf[slot] = y;
-                    fa[slot] = entry_value(P, La, sa, dmin2, g);
-                    fb[slot] = vb[j];
+                const int nf = na + nb - common;
+                __syncwarp(gmask);
+                const float rq = p_is_a ? __fdiv_rn(Ib, Ia) : __fdiv_rn(Ia, Ib);
+                float e = 0.f;
+                for (int i = gl; i < nf; i += GS) {
+                    const float vp = p_is_a ? fa[i] : fb[i];
+                    const float vq = p_is_a ? fb[i] : fa[i];
+                    e = fmaxf(e, fabsf(vq - vp * rq));
                 }
-                seen += __popc(bal);
-            }
-            const int nf = na + nb - common;
-            __syncwarp();
-            const float rq = p_is_a ? __fdiv_rn(Ib, Ia) : __fdiv_rn(Ia, Ib);
-            float e = 0.f;
-            for (int i = lane; i < nf; i += 32) {
-                const float vp = p_is_a ? fa[i] : fb[i];
-                const float vq = p_is_a ? fb[i] : fa[i];
-                e = fmaxf(e, fabsf(vq - vp * rq));
-            }
-            e = warp_max(e);
-            const int q = p_is_a ? b : a;
-            const float cf = e + cost[q];
-            const bool merge = cf < thr;
-            if (merge) {
-                const float rfp = __fdiv_rn(If, p_is_a ? Ia : Ib);
-                for (int i = lane; i < nf; i += 32) fa[i] = (p_is_a ? fa[i] : fb[i]) * rfp;
-            }
-            if (lane == 0) {
-                cnt[f] = nf;
-                cost[f] = cf;
-                state[f] = merge ? kStAlive : kStRejected;
+#pragma unroll
+                for (int o = GS / 2; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(gmask, e, o, GS));
+                const int q = p_is_a ? b : a;
+                const float cf = e + cost[q];
+                const bool merge = cf < thr;
                 if (merge) {
-                    state[a] = kStDead;
-                    state[b] = kStDead;
+                    const float rfp = __fdiv_rn(If, p_is_a ? Ia : Ib);
+                    for (int i = gl; i < nf; i += GS) fa[i] = (p_is_a ? fa[i] : fb[i]) * rfp;
                 }
+                if (gl == 0) {
+                    cnt[f] = nf;
+                    cost[f] = cf;
+                    state[f] = merge ? kStAlive : kStRejected;
+                    if (merge) {
+                        state[a] = kStDead;
+                        state[b] = kStDead;
+                    }
+                }
+                __syncwarp(gmask);
             }
-            __syncwarp();
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // -- D: the coarsened cut in leaf order and its observed entries
