@@ -201,7 +201,9 @@ __device__ __forceinline__ void gram_tc(int len, const uint16_t* __restrict__ id
     for (int e0 = 0; e0 < len; e0 += 32) {
         const int je = e0 + lane < len ? (int)idx[e0 + lane] : -1;
         const float ae = e0 + lane < len ? val[e0 + lane] : 0.f;
-        for (int q = 0; q < 4 && e0 + 8 * q < len; ++q) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (e0 + 8 * q >= len) break;  // uniform in the warp
             const int j0 = __shfl_sync(FULL, je, 8 * q + t), j1 = __shfl_sync(FULL, je, 8 * q + t + 4);
             const float a0v = __shfl_sync(FULL, ae, 8 * q + t), a1v = __shfl_sync(FULL, ae, 8 * q + t + 4);
             // x[mt][0] = X[t][16mt+g], [1] = X[t][16mt+g+8], [2] = X[t+4][16mt+g], [3] = X[t+4][16mt+g+8]
@@ -487,9 +489,22 @@ __global__ void __launch_bounds__(512, 1) k_gram16(lt_frame F, lt_samples smp, O
     const int nsrc = rows_side ? ns : ms;
     const bool staged = nsrc <= stage_rows;
     if (staged) {
-        for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
-            const int row = i / RP, c = i % RP;
-            stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * r + c) : 0.f;
+        if (r == RP) {  // 16-byte loads of whole factor rows
+            const float4* src4 = reinterpret_cast<const float4*>(src);
+            for (int i = threadIdx.x; i < nsrc * (RP / 4); i += blockDim.x) {
+                const int row = i / (RP / 4), c4 = i % (RP / 4);
+                const float4 v = __ldg(src4 + i);
+                float* d = stage + row * (RP + 1) + 4 * c4;
+                d[0] = v.x;
+                d[1] = v.y;
+                d[2] = v.z;
+                d[3] = v.w;
+            }
+        } else {
+            for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
+                const int row = i / RP, c = i % RP;
+                stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * r + c) : 0.f;
+            }
         }
     }
     __syncthreads();

@@ -209,6 +209,7 @@ extern "C" lt_status lt_scene_upload(lt_ctx* ctx, const float* boxes, int64_t nb
     g.cell_box = ctx->d_cell_box;
     g.nb = (int)nb;
     g.R = R;
+    g.nlist = (int)(count[ncell]);
     for (int a = 0; a < 3; ++a) {
         g.lo[a] = lo[a];
         g.cell[a] = cell[a];

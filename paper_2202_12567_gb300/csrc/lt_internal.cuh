@@ -72,6 +72,7 @@ struct Grid {
     const int32_t* cell_box; // [cell_off[R^3]]
     int nb;
     int R;
+    int nlist;               // entries of cell_box
     float lo[3];
     float cell[3];
     float inv_cell[3];
@@ -80,9 +81,9 @@ struct Grid {
 // Closed-box slab test of o + t D over t in [kTMin, kTMax].
 __device__ __forceinline__ bool slab_hit(const float* __restrict__ b, float3 o, float3 inv, int par) {
     float tn = kTMin, tf = kTMax;
-    const float2 b01 = __ldg(reinterpret_cast<const float2*>(b));
-    const float2 b23 = __ldg(reinterpret_cast<const float2*>(b) + 1);
-    const float2 b45 = __ldg(reinterpret_cast<const float2*>(b) + 2);
+    const float2 b01 = reinterpret_cast<const float2*>(b)[0];
+    const float2 b23 = reinterpret_cast<const float2*>(b)[1];
+    const float2 b45 = reinterpret_cast<const float2*>(b)[2];
     const float lo0 = b01.x, lo1 = b01.y, lo2 = b23.x, hi0 = b23.y, hi1 = b45.x, hi2 = b45.y;
     if (par & 1) {
         if (o.x < lo0 || o.x > hi0) return false;
@@ -162,10 +163,10 @@ __device__ inline bool seg_blocked(const Grid& g, float3 o, float3 e, WorkCount*
     const int max_steps = 3 * R + 3;
     for (int it = 0; it < max_steps; ++it) {
         const int cell = (c[2] * R + c[1]) * R + c[0];
-        const int b0 = __ldg(g.cell_off + cell), b1 = __ldg(g.cell_off + cell + 1);
+        const int b0 = g.cell_off[cell], b1 = g.cell_off[cell + 1];
         if (COUNT) ++wc->cells;
         for (int k = b0; k < b1; ++k) {
-            const int bi = __ldg(g.cell_box + k);
+            const int bi = g.cell_box[k];
             if (COUNT) ++wc->boxes;
             if (slab_hit(g.box + 6 * bi, o, inv, par)) return true;
         }
@@ -199,11 +200,46 @@ struct PointRec {
     float4 a, b, c;   // [p albedo] [n gloss] [wo 0]
 };
 
+// Bytes of shared memory that staging the grid takes (0 if there is no grid).
+__host__ __device__ inline int grid_stage_bytes(const Grid& g) {
+    if (g.nb == 0) return 0;
+    const int cells = g.R * g.R * g.R + 1;
+    return ((cells + g.nlist) * 4 + 15) / 16 * 16 + g.nb * 24;
+}
+
+// Copy the grid into shared memory at `smem` (16-byte aligned) with the whole block
+// and return a Grid that points there.  Call with every thread of the block, then
+// __syncthreads() before use.
+__device__ inline Grid stage_grid(const Grid& g, char* smem) {
+    Grid s = g;
+    if (g.nb == 0) return s;
+    const int cells = g.R * g.R * g.R + 1;
+    int32_t* off = reinterpret_cast<int32_t*>(smem);
+    int32_t* lst = off + cells;
+    float* box = reinterpret_cast<float*>(smem + ((cells + g.nlist) * 4 + 15) / 16 * 16);
+    for (int i = threadIdx.x; i < cells; i += blockDim.x) off[i] = g.cell_off[i];
+    for (int i = threadIdx.x; i < g.nlist; i += blockDim.x) lst[i] = g.cell_box[i];
+    for (int i = threadIdx.x; i < g.nb * 6; i += blockDim.x) box[i] = g.box[i];
+    s.cell_off = off;
+    s.cell_box = lst;
+    s.box = box;
+    return s;
+}
+
 __device__ __forceinline__ PointRec load_rec(const float4* __restrict__ planes, int64_t count, int64_t i) {
     PointRec r;
     r.a = __ldg(planes + i);
     r.b = __ldg(planes + count + i);
     r.c = __ldg(planes + 2 * count + i);
+    return r;
+}
+
+// The same from a generic (global or shared) pointer.
+__device__ __forceinline__ PointRec load_rec_any(const float4* planes, int64_t count, int64_t i) {
+    PointRec r;
+    r.a = planes[i];
+    r.b = planes[count + i];
+    r.c = planes[2 * count + i];
     return r;
 }
 

@@ -24,7 +24,10 @@ using namespace ltk;
 namespace {
 
 constexpr int kP1Threads = 512;
-constexpr int kPairLanes = 8;   // lanes per sibling-pair test
+constexpr int kPairLanes = 8;   // lanes per sibling-pair test of a large pair
+constexpr int kSmallPair = 16;  // pairs with at most this many rows are tested by one thread
+constexpr int kBigQueue = 4096;
+constexpr int kHugePair = 128;  // pairs with more rows are tested by the whole block
 constexpr int kP2Threads = 1024;
 constexpr int kMaxRowsPerNode = 64;
 constexpr int kMaxDraws = 1 << 16;
@@ -99,36 +102,436 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_plan(lt_frame F, float rat
     if (threadIdx.x == 0) pl.total[s] = tot;
 }
 
-// ------------------------------------------------------------------ pass 1: main
+// ------------------------------------------------------------------ pass 1: flat kernels
+// Every kernel below runs over all slices at once.  Per forest level: k_p1_setup
+// lays out the union of each testable sibling pair and queues the entries it lacks,
+// k_p1_rays evaluates the queue (one shadow ray per thread), k_p1_decide reduces
+// eps, applies Eq. 2 and merges or rejects.  Pairs with more than kThreadPair rows
+// are laid out and decided by a warp each.
+constexpr int kThreadPair = 64;
+
 struct P1Store {
-    int32_t* rows;
-    float* v0;
-    float* v1;
+    int32_t* rows;     // [total] row of each storage slot
+    float* v0;         // [total]  (V_a, or V_f after a merge)
+    float* v1;         // [total]  (V_b), == v0 + total
+    int64_t total;
 };
 
-__global__ void __launch_bounds__(kP1Threads) k_pass1(lt_frame F, Grid g, float rate, float tau, float dmin2,
-                                                      uint64_t seed, P1Plan pl, P1Store st, lt_samples smp,
-                                                      int32_t* status) {
-    extern __shared__ int32_t sh[];                 // [C+1] prefix of k
-    __shared__ int32_t ws[32];
-    __shared__ float red[32];
-    __shared__ float s_thr;
-    const int s = blockIdx.x;
+struct P1Work {
+    int64_t* kpfx;     // [S+1] prefix over slices of the initial entry counts
+    float* leafmean;   // [S][C] mean of each cut node's initial entries
+    float* thr;        // [S] tau * S_hat
+    int64_t* mcount;   // [Hmax] queued missing entries per level
+    int64_t* bcount;   // [Hmax] big pairs per level
+    int64_t* mdst;     // [mcap] flat value index (v0 or v1) of a missing entry
+    int32_t* mpt;      // [mcap] slice-ordered point of the entry
+    int32_t* mnode;    // [mcap] tree node of the entry's column
+    int64_t* big;      // [bcap] flat pair index of a big pair
+    int64_t mcap, bcap;
+};
+
+// -- draws of the cut nodes and state of every forest node
+__global__ void k_p1_draws(lt_frame F, uint64_t seed, P1Plan pl, P1Store st, int32_t* status) {
     const int C = F.C, NF = 2 * C - 1;
-    const int row0 = F.slice_off[s];
-    const int ms = F.slice_off[s + 1] - row0;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)F.S * NF;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / NF), x = (int)(idx % NF);
+        const int ms = F.slice_off[s + 1] - F.slice_off[s];
+        int32_t* cnt = pl.cnt + (int64_t)s * NF;
+        int32_t* state = pl.state + (int64_t)s * NF;
+        float* cost = pl.cost + (int64_t)s * NF;
+        cost[x] = 0.f;
+        if (x >= C) {
+            cnt[x] = 0;
+            state[x] = kStNot;
+            continue;
+        }
+        const int k = pl.k[(int64_t)s * C + x];
+        int32_t* r = st.rows + pl.base[s] + pl.off[(int64_t)s * NF + x];
+        int got = 0;
+        if (k >= ms) {
+            for (int t = 0; t < ms; ++t) r[t] = t;
+            got = ms;
+        } else {
+            for (int t = 0; got < k && t < kMaxDraws; ++t) {
+                const int v = (int)uniform_index(philox((uint32_t)t, (uint32_t)x, (uint32_t)s, kTagPass1, seed).x,
+                                                 (uint32_t)ms);
+                bool dup = false;
+                for (int q = 0; q < got; ++q) dup |= (r[q] == v);
+                if (!dup) r[got++] = v;
+            }
+            if (got < k) latch(status, LT_ELIMIT);
+            for (int a = 1; a < got; ++a) {  // insertion sort, got <= 64
+                const int v = r[a];
+                int b = a - 1;
+                while (b >= 0 && r[b] > v) {
+                    r[b + 1] = r[b];
+                    --b;
+                }
+                r[b + 1] = v;
+            }
+        }
+        cnt[x] = got;
+        state[x] = ms > 0 ? kStAlive : kStNot;
+    }
+}
+
+__global__ void k_p1_kpfx(lt_frame F, P1Plan pl, int64_t* kpfx) {
+    __shared__ int64_t ws[32];
+    int64_t carry = 0;
+    for (int c0 = 0; c0 < F.S; c0 += blockDim.x) {
+        const int s = c0 + threadIdx.x;
+        const int64_t x = s < F.S ? (int64_t)pl.pfx[(int64_t)s * (F.C + 1) + F.C] : 0;
+        int64_t tot;
+        const int64_t pre = block_exclusive_scan<int64_t>(x, ws, &tot);
+        if (s < F.S) kpfx[s] = carry + pre;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) kpfx[F.S] = carry;
+}
+
+// -- initial entries of every cut node of every slice (one shadow ray per thread)
+__global__ void __launch_bounds__(128) k_p1_initial(lt_frame F, Grid g, float dmin2, P1Plan pl, P1Store st,
+                                                    const int64_t* __restrict__ kpfx) {
     const float4* pts = reinterpret_cast<const float4*>(F.pts);
     const float4* vpls = reinterpret_cast<const float4*>(F.vpls);
-    const int32_t* kk = pl.k + (int64_t)s * C;
+    const int C = F.C, NF = 2 * C - 1;
+    const int64_t total = kpfx[F.S];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = F.S;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (kpfx[mid] <= idx) lo = mid;
+            else hi = mid;
+        }
+        const int s = lo;
+        const int e = (int)(idx - kpfx[s]);
+        const int32_t* pf = pl.pfx + (int64_t)s * (C + 1);
+        int a = 0, b = C;  // largest c with pf[c] <= e
+        while (b - a > 1) {
+            const int mid = (a + b) >> 1;
+            if (pf[mid] <= e) a = mid;
+            else b = mid;
+        }
+        const int c = a, t = e - pf[c];
+        const int64_t slot = pl.base[s] + pl.off[(int64_t)s * NF + c] + t;
+        const int node = F.forest[8 * c];
+        const PointRec P = load_rec(pts, F.m, F.slice_off[s] + st.rows[slot]);
+        const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
+        st.v0[slot] = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
+    }
+}
+
+__global__ void k_p1_leafmean(lt_frame F, P1Plan pl, P1Store st, float* leafmean) {
+    const int C = F.C, NF = 2 * C - 1;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)F.S * C;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(idx / C), c = (int)(idx % C);
+        const int n = pl.cnt[(int64_t)s * NF + c];
+        const float* v = st.v0 + pl.base[s] + pl.off[(int64_t)s * NF + c];
+        float sum = 0.f;
+        for (int t = 0; t < n; ++t) sum += v[t];
+        leafmean[idx] = n > 0 ? sum / (float)n : 0.f;
+    }
+}
+
+// tau * S_hat per slice, S_hat = sum_c mean(V_c) (fixed reduction order)
+__global__ void k_p1_thr(lt_frame F, const float* __restrict__ leafmean, float tau, float* thr) {
+    __shared__ float red[32];
+    const int s = blockIdx.x;
+    float sum = 0.f;
+    for (int c = threadIdx.x; c < F.C; c += blockDim.x) sum += leafmean[(int64_t)s * F.C + c];
+    sum = warp_sum(sum);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        thr[s] = tau * t;
+    }
+}
+
+struct PairCtx {
+    int s, f, a, b, na, nb, row0;
+    int64_t base;
+    const int32_t* ra;
+    const int32_t* rb;
+    int64_t ia, ib, iff;   // storage offsets of a, b, f inside the slice's region
+};
+
+__device__ __forceinline__ bool load_pair(const lt_frame& F, const P1Plan& pl, const P1Store& st, int h, int64_t t,
+                                          PairCtx& pc) {
+    const int l0 = F.level_off[h], np = F.level_off[h + 1] - l0;
+    const int NF = 2 * F.C - 1;
+    pc.s = (int)(t / np);
+    pc.f = F.level_nodes[l0 + (int)(t % np)];
+    pc.a = F.forest[8 * pc.f + 1];
+    pc.b = F.forest[8 * pc.f + 2];
+    const int32_t* state = pl.state + (int64_t)pc.s * NF;
+    if (state[pc.a] != kStAlive || state[pc.b] != kStAlive) return false;
+    const int32_t* cnt = pl.cnt + (int64_t)pc.s * NF;
+    const int32_t* off = pl.off + (int64_t)pc.s * NF;
+    pc.na = cnt[pc.a];
+    pc.nb = cnt[pc.b];
+    pc.base = pl.base[pc.s];
+    pc.ia = pc.base + off[pc.a];
+    pc.ib = pc.base + off[pc.b];
+    pc.iff = pc.base + off[pc.f];
+    pc.ra = st.rows + pc.ia;
+    pc.rb = st.rows + pc.ib;
+    pc.row0 = F.slice_off[pc.s];
+    return true;
+}
+
+// Reserve n queue slots for each lane of the warp with one atomic per warp; returns
+// this lane's first slot.  Every lane of the warp must call it.
+__device__ __forceinline__ long long warp_reserve(unsigned long long* counter, int n) {
+    const int lane = threadIdx.x & 31;
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned long long base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(counter, (unsigned long long)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return (long long)base + (incl - n);
+}
+
+__device__ __forceinline__ void put_missing(const P1Work& w, long long q, int64_t dst, int pt, int node,
+                                            int32_t* status) {
+    if (q < w.mcap) {
+        w.mdst[q] = dst;
+        w.mpt[q] = pt;
+        w.mnode[q] = node;
+    } else {
+        latch(status, LT_ELIMIT);
+    }
+}
+
+// -- level h, step 1: union layout of every testable pair, queue of missing entries
+__global__ void k_p1_setup(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h, int32_t* status) {
+    const int np = F.level_off[h + 1] - F.level_off[h];
+    const int NF = 2 * F.C - 1;
+    const int64_t npairs = (int64_t)F.S * np;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count so that every lane takes part in the reservations
+    for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < npairs; t0 += stride) {
+        const int64_t t = t0 + threadIdx.x;
+        PairCtx pc;
+        bool active = t < npairs && load_pair(F, pl, st, h, t, pc);
+        const bool big = active && pc.na + pc.nb > kThreadPair;
+        const long long qb = warp_reserve((unsigned long long*)&w.bcount[h], big ? 1 : 0);
+        if (big) {
+            if (qb < w.bcap) w.big[qb] = t;
+            else latch(status, LT_ELIMIT);
+            active = false;
+        }
+        // count the missing entries (rows in only one of the two sets)
+        int nmiss = 0;
+        if (active) {
+            int i = 0, j = 0;
+            while (i < pc.na || j < pc.nb) {
+                const int xa = i < pc.na ? pc.ra[i] : 0x7fffffff, xb = j < pc.nb ? pc.rb[j] : 0x7fffffff;
+                if (xa < xb) ++i, ++nmiss;
+                else if (xb < xa) ++j, ++nmiss;
+                else ++i, ++j;
+            }
+        }
+        long long q = warp_reserve((unsigned long long*)&w.mcount[h], nmiss);
+        if (!active) continue;
+        const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b];
+        int32_t* rf = st.rows + pc.iff;
+        float* fa = st.v0 + pc.iff;
+        float* fb = st.v1 + pc.iff;
+        int i = 0, j = 0, n = 0;
+        while (i < pc.na || j < pc.nb) {
+            const int xa = i < pc.na ? pc.ra[i] : 0x7fffffff, xb = j < pc.nb ? pc.rb[j] : 0x7fffffff;
+            if (xa < xb) {
+                rf[n] = xa;
+                fa[n] = st.v0[pc.ia + i++];
+                put_missing(w, q++, st.total + pc.iff + n, pc.row0 + xa, tb, status);   // V_b(xa)
+            } else if (xb < xa) {
+                rf[n] = xb;
+                fb[n] = st.v0[pc.ib + j++];
+                put_missing(w, q++, pc.iff + n, pc.row0 + xb, ta, status);              // V_a(xb)
+            } else {
+                rf[n] = xa;
+                fa[n] = st.v0[pc.ia + i++];
+                fb[n] = st.v0[pc.ib + j++];
+            }
+            ++n;
+        }
+        pl.cnt[(int64_t)pc.s * NF + pc.f] = n;
+    }
+}
+
+// the same for pairs with more than kThreadPair rows, one warp per pair
+__global__ void k_p1_setup_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h, int32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int NF = 2 * F.C - 1;
+    const int64_t nbig = min(w.bcount[h], w.bcap);
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nbig;
+         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        PairCtx pc;
+        load_pair(F, pl, st, h, w.big[q], pc);
+        const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b];
+        int32_t* rf = st.rows + pc.iff;
+        float* fa = st.v0 + pc.iff;
+        float* fb = st.v1 + pc.iff;
+        int common = 0;
+        for (int i0 = 0; i0 < pc.na; i0 += 32) {
+            const int i = i0 + lane;
+            int x = 0, pb = 0;
+            bool both = false;
+            if (i < pc.na) {
+                x = pc.ra[i];
+                pb = lower_bound<int32_t>(pc.rb, pc.nb, x);
+                both = pb < pc.nb && pc.rb[pb] == x;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, both);
+            const long long m = warp_reserve((unsigned long long*)&w.mcount[h], (i < pc.na && !both) ? 1 : 0);
+            if (i < pc.na) {
+                const int slot = i + pb - (common + __popc(bal & lt_mask));
+                rf[slot] = x;
+                fa[slot] = st.v0[pc.ia + i];
+                if (both) fb[slot] = st.v0[pc.ib + pb];
+                else put_missing(w, m, st.total + pc.iff + slot, pc.row0 + x, tb, status);
+            }
+            common += __popc(bal);
+        }
+        int seen = 0;
+        for (int j0 = 0; j0 < pc.nb; j0 += 32) {
+            const int j = j0 + lane;
+            int y = 0, pa = 0;
+            bool both = false;
+            if (j < pc.nb) {
+                y = pc.rb[j];
+                pa = lower_bound<int32_t>(pc.ra, pc.na, y);
+                both = pa < pc.na && pc.ra[pa] == y;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, both);
+            const long long m = warp_reserve((unsigned long long*)&w.mcount[h], (j < pc.nb && !both) ? 1 : 0);
+            if (j < pc.nb && !both) {
+                const int slot = j + pa - (seen + __popc(bal & lt_mask));
+                rf[slot] = y;
+                fb[slot] = st.v0[pc.ib + j];
+                put_missing(w, m, pc.iff + slot, pc.row0 + y, ta, status);
+            }
+            seen += __popc(bal);
+        }
+        if (lane == 0) pl.cnt[(int64_t)pc.s * NF + pc.f] = pc.na + pc.nb - common;
+    }
+}
+
+// -- level h, step 2: the queued entries, one shadow ray per thread
+__global__ void __launch_bounds__(128) k_p1_rays(lt_frame F, Grid g, float dmin2, P1Store st, P1Work w, int h) {
+    const float4* pts = reinterpret_cast<const float4*>(F.pts);
+    const float4* vpls = reinterpret_cast<const float4*>(F.vpls);
+    const int64_t n = min(w.mcount[h], w.mcap);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int node = w.mnode[q];
+        const PointRec P = load_rec(pts, F.m, w.mpt[q]);
+        const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
+        st.v0[w.mdst[q]] = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
+    }
+}
+
+// -- level h, step 3: eps (Sec. 4), cost (Eq. 2), merge or reject
+__device__ __forceinline__ void decide_pair(const lt_frame& F, const P1Plan& pl, const P1Store& st, const float* thr,
+                                            const PairCtx& pc, float e_max, int first, int step, bool writer) {
+    const int NF = 2 * F.C - 1;
+    const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b], tf = F.forest[8 * pc.f];
+    const float Ia = F.tree.I[ta], Ib = F.tree.I[tb], If = F.tree.I[tf];
+    const bool p_is_a = Ia >= Ib;
+    float* cost = pl.cost + (int64_t)pc.s * NF;
+    int32_t* state = pl.state + (int64_t)pc.s * NF;
+    const int q = p_is_a ? pc.b : pc.a;
+    const float cf = e_max + cost[q];
+    const bool merge = cf < thr[pc.s];
+    const int nf = pl.cnt[(int64_t)pc.s * NF + pc.f];
+    if (merge) {
+        const float rfp = __fdiv_rn(If, p_is_a ? Ia : Ib);
+        float* fa = st.v0 + pc.iff;
+        const float* fb = st.v1 + pc.iff;
+        for (int t = first; t < nf; t += step) fa[t] = (p_is_a ? fa[t] : fb[t]) * rfp;
+    }
+    if (writer) {
+        cost[pc.f] = cf;
+        state[pc.f] = merge ? kStAlive : kStRejected;
+        if (merge) {
+            state[pc.a] = kStDead;
+            state[pc.b] = kStDead;
+        }
+    }
+}
+
+__device__ __forceinline__ float pair_eps(const lt_frame& F, const P1Store& st, const PairCtx& pc, int nf, int lane,
+                                          int step) {
+    const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b];
+    const float Ia = F.tree.I[ta], Ib = F.tree.I[tb];
+    const bool p_is_a = Ia >= Ib;
+    const float rq = p_is_a ? __fdiv_rn(Ib, Ia) : __fdiv_rn(Ia, Ib);
+    const float* fa = st.v0 + pc.iff;
+    const float* fb = st.v1 + pc.iff;
+    float e = 0.f;
+    for (int t = lane; t < nf; t += step) {
+        const float vp = p_is_a ? fa[t] : fb[t];
+        const float vq = p_is_a ? fb[t] : fa[t];
+        e = fmaxf(e, fabsf(vq - vp * rq));
+    }
+    return e;
+}
+
+__global__ void k_p1_decide(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+    const int np = F.level_off[h + 1] - F.level_off[h];
+    const int NF = 2 * F.C - 1;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)F.S * np;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        PairCtx pc;
+        if (!load_pair(F, pl, st, h, t, pc)) continue;
+        if (pc.na + pc.nb > kThreadPair) continue;
+        const int nf = pl.cnt[(int64_t)pc.s * NF + pc.f];
+        decide_pair(F, pl, st, w.thr, pc, pair_eps(F, st, pc, nf, 0, 1), 0, 1, true);
+    }
+}
+
+__global__ void k_p1_decide_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+    const int lane = threadIdx.x & 31;
+    const int NF = 2 * F.C - 1;
+    const int64_t nbig = min(w.bcount[h], w.bcap);
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nbig;
+         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        PairCtx pc;
+        load_pair(F, pl, st, h, w.big[q], pc);
+        const int nf = pl.cnt[(int64_t)pc.s * NF + pc.f];
+        const float e = warp_max(pair_eps(F, st, pc, nf, lane, 32));
+        __syncwarp();
+        decide_pair(F, pl, st, w.thr, pc, e, lane, 32, lane == 0);
+    }
+}
+
+// -- the coarsened cut of every slice in leaf order and its observed entries
+__global__ void __launch_bounds__(kP1Threads) k_p1_output(lt_frame F, P1Plan pl, P1Store st, lt_samples smp,
+                                                          int32_t* status) {
+    extern __shared__ int32_t mark[];  // [C] forest node whose first leaf is c, else -1
+    __shared__ int32_t ws[32];
+    __shared__ float red[32];
+    const int s = blockIdx.x;
+    const int C = F.C, NF = 2 * C - 1;
+    const int ms = F.slice_off[s + 1] - F.slice_off[s];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int32_t* off = pl.off + (int64_t)s * NF;
-    int32_t* cnt = pl.cnt + (int64_t)s * NF;
-    int32_t* state = pl.state + (int64_t)s * NF;
-    float* cost = pl.cost + (int64_t)s * NF;
+    const int32_t* cnt = pl.cnt + (int64_t)s * NF;
+    const int32_t* state = pl.state + (int64_t)s * NF;
     const int64_t base = pl.base[s];
-    int32_t* rows = st.rows + base;
-    float* v0 = st.v0 + base;
-    float* v1 = st.v1 + base;
+    const int32_t* rows = st.rows + base;
+    const float* v0 = st.v0 + base;
+    const float* v1 = st.v1 + base;
     if (ms == 0) {
         if (threadIdx.x == 0) {
             smp.ncol[s] = 0;
@@ -137,189 +540,6 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1(lt_frame F, Grid g, float 
         }
         return;
     }
-    for (int i = threadIdx.x; i <= C; i += blockDim.x) sh[i] = pl.pfx[(int64_t)s * (C + 1) + i];
-
-    // -- A: rows per cut node, first k distinct Philox draws, sorted ascending
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        const int k = kk[c];
-        int32_t* r = rows + off[c];
-        int got = 0;
-        if (k >= ms) {
-            for (int t = 0; t < ms; ++t) r[t] = t;
-            got = ms;
-        } else {
-            for (int t = 0; got < k && t < kMaxDraws; ++t) {
-                const int x = (int)uniform_index(philox((uint32_t)t, (uint32_t)c, (uint32_t)s, kTagPass1, seed).x,
-                                                 (uint32_t)ms);
-                bool dup = false;
-                for (int q = 0; q < got; ++q) dup |= (r[q] == x);
-                if (!dup) r[got++] = x;
-            }
-            if (got < k) latch(status, LT_ELIMIT);
-            for (int a = 1; a < got; ++a) {  // insertion sort, got <= 64
-                const int x = r[a];
-                int b = a - 1;
-                while (b >= 0 && r[b] > x) {
-                    r[b + 1] = r[b];
-                    --b;
-                }
-                r[b + 1] = x;
-            }
-        }
-        cnt[c] = got;
-        state[c] = kStAlive;
-        cost[c] = 0.f;
-    }
-    for (int x = C + threadIdx.x; x < NF; x += blockDim.x) {
-        cnt[x] = 0;
-        state[x] = kStNot;
-        cost[x] = 0.f;
-    }
-    __syncthreads();
-
-    // -- B: initial entries of every cut node; S_hat = sum_c mean(V_c)
-    const int K = sh[C];
-    float part = 0.f;
-    for (int idx = threadIdx.x; idx < K; idx += blockDim.x) {
-        int lo = 0, hi = C;  // largest c with sh[c] <= idx
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (sh[mid] <= idx) lo = mid;
-            else hi = mid;
-        }
-        const int c = lo, t = idx - sh[c];
-        const int node = F.forest[8 * c];
-        const int r = rows[off[c] + t];
-        const PointRec P = load_rec(pts, F.m, row0 + r);
-        const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
-        const float v = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
-        v0[off[c] + t] = v;
-        part += v / (float)kk[c];
-    }
-    part = warp_sum(part);
-    if (lane == 0) red[wid] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float shat = 0.f;
-        for (int w = 0; w < nw; ++w) shat += red[w];
-        s_thr = tau * shat;
-    }
-    __syncthreads();
-    const float thr = s_thr;
-
-    // -- C: coarsening, one forest level per round, one group of kPairLanes lanes per
-    //       sibling pair (most pairs union only a few rows)
-    {
-        constexpr int GS = kPairLanes;
-        const int grp = lane / GS, gl = lane % GS;
-        const unsigned gmask = ((GS == 32) ? 0xffffffffu : ((1u << GS) - 1u)) << (grp * GS);
-        const unsigned lt_mask = (1u << gl) - 1u;
-        const int ngroups = nw * (32 / GS), gid = wid * (32 / GS) + grp;
-        for (int h = 1; h <= F.H; ++h) {
-            const int l0 = F.level_off[h], l1 = F.level_off[h + 1];
-            for (int li = l0 + gid; li < l1; li += ngroups) {
-                const int f = F.level_nodes[li];
-                const int* fx = F.forest + 8 * f;
-                const int a = fx[1], b = fx[2];
-                if (state[a] != kStAlive || state[b] != kStAlive) continue;  // uniform in the group
-                const int ta = F.forest[8 * a], tb = F.forest[8 * b], tf = fx[0];
-                const float Ia = F.tree.I[ta], Ib = F.tree.I[tb], If = F.tree.I[tf];
-                const bool p_is_a = Ia >= Ib;
-                const int na = cnt[a], nb = cnt[b];
-                const int32_t* ra = rows + off[a];
-                const int32_t* rb = rows + off[b];
-                const float* va = v0 + off[a];
-                const float* vb = v0 + off[b];
-                int32_t* rf = rows + off[f];
-                float* fa = v0 + off[f];
-                float* fb = v1 + off[f];
-                const float sa = node_scale(F.tree, vpls, F.n, ta), sb = node_scale(F.tree, vpls, F.n, tb);
-                const PointRec La = load_rec(vpls, F.n, F.tree.rep[ta]);
-                const PointRec Lb = load_rec(vpls, F.n, F.tree.rep[tb]);
-                // Union of two sorted row sets: the slot of a row is the number of
-                // distinct rows below it, i.e. (rows of a below) + (rows of b below) -
-                // (rows in both below); the last term is a running ballot count.
-                int common = 0;
-                for (int i0 = 0; i0 < na; i0 += GS) {
-                    const int i = i0 + gl;
-                    int x = 0, pb = 0;
-                    bool both = false;
-                    if (i < na) {
-                        x = ra[i];
-                        pb = lower_bound<int32_t>(rb, nb, x);
-                        both = pb < nb && rb[pb] == x;
-                    }
-                    const unsigned bal = (__ballot_sync(gmask, both) >> (grp * GS)) & (gmask >> (grp * GS));
-                    if (i < na) {
-                        const int slot = i + pb - (common + __popc(bal & lt_mask));
-                        float xb;
-                        if (both) {
-                            xb = vb[pb];
-                        } else {
-                            const PointRec P = load_rec(pts, F.m, row0 + x);
-                            xb = entry_value(P, Lb, sb, dmin2, g);
-                        }
-                        rf[slot] = x;
-                        fa[slot] = va[i];
-                        fb[slot] = xb;
-                    }
-                    common += __popc(bal);
-                }
-                int seen = 0;  // rows of b (so far) that are also in a
-                for (int j0 = 0; j0 < nb; j0 += GS) {
-                    const int j = j0 + gl;
-                    int y = 0, pa = 0;
-                    bool both = false;
-                    if (j < nb) {
-                        y = rb[j];
-                        pa = lower_bound<int32_t>(ra, na, y);
-                        both = pa < na && ra[pa] == y;
-                    }
-                    const unsigned bal = (__ballot_sync(gmask, both) >> (grp * GS)) & (gmask >> (grp * GS));
-                    if (j < nb && !both) {
-                        const int slot = j + pa - (seen + __popc(bal & lt_mask));
-                        const PointRec P = load_rec(pts, F.m, row0 + y);
-                        rf[slot] = y;
-                        fa[slot] = entry_value(P, La, sa, dmin2, g);
-                        fb[slot] = vb[j];
-                    }
-                    seen += __popc(bal);
-                }
-                const int nf = na + nb - common;
-                __syncwarp(gmask);
-                const float rq = p_is_a ? __fdiv_rn(Ib, Ia) : __fdiv_rn(Ia, Ib);
-                float e = 0.f;
-                for (int i = gl; i < nf; i += GS) {
-                    const float vp = p_is_a ? fa[i] : fb[i];
-                    const float vq = p_is_a ? fb[i] : fa[i];
-                    e = fmaxf(e, fabsf(vq - vp * rq));
-                }
-#pragma unroll
-                for (int o = GS / 2; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(gmask, e, o, GS));
-                const int q = p_is_a ? b : a;
-                const float cf = e + cost[q];
-                const bool merge = cf < thr;
-                if (merge) {
-                    const float rfp = __fdiv_rn(If, p_is_a ? Ia : Ib);
-                    for (int i = gl; i < nf; i += GS) fa[i] = (p_is_a ? fa[i] : fb[i]) * rfp;
-                }
-                if (gl == 0) {
-                    cnt[f] = nf;
-                    cost[f] = cf;
-                    state[f] = merge ? kStAlive : kStRejected;
-                    if (merge) {
-                        state[a] = kStDead;
-                        state[b] = kStDead;
-                    }
-                }
-                __syncwarp(gmask);
-            }
-            __syncthreads();
-        }
-    }
-
-    // -- D: the coarsened cut in leaf order and its observed entries
-    int32_t* mark = sh;  // reuse: [C] forest node whose first leaf is c, else -1
     for (int c = threadIdx.x; c < C; c += blockDim.x) mark[c] = -1;
     __syncthreads();
     for (int x = threadIdx.x; x < NF; x += blockDim.x)
@@ -344,7 +564,6 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1(lt_frame F, Grid g, float 
         ncol += tot;
     }
     __syncthreads();
-    // entry counts -> offsets (in place)
     int n1 = 0;
     for (int c0 = 0; c0 < ncol; c0 += blockDim.x) {
         const int j = c0 + threadIdx.x;
@@ -669,18 +888,80 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
         acc += tot[s];
     }
     LT_CUDA(ctx, cudaMemcpyAsync(pl.base, basev.data(), S * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-    char* q = (char*)lt_scratch(ctx, SCR_P1_STORE, (size_t)std::max<int64_t>(acc, 1) * 12 + 1024, &st);
+    // storage: rows, then v0 and v1 back to back (a flat value index addresses both);
+    // then the work arrays of the flat kernels
+    const int Hn = f->H + 2;
+    const int64_t mcap = std::max<int64_t>(acc, 1024), bcap = std::max<int64_t>((int64_t)S * C, 1024);
+    const size_t store_bytes = (size_t)std::max<int64_t>(acc, 1) * 12 + 1024;
+    const size_t work_bytes = (size_t)(S + 1) * 8 + (size_t)S * C * 4 + (size_t)S * 4 + (size_t)Hn * 16 +
+                              (size_t)mcap * 16 + (size_t)bcap * 8 + 16 * 256;
+    char* q = (char*)lt_scratch(ctx, SCR_P1_STORE, store_bytes + work_bytes, &st);
     if (!q) return st;
     P1Store store;
+    store.total = acc;
     store.rows = (int32_t*)q;
     store.v0 = (float*)(q + ((acc * 4 + 255) & ~255LL));
-    store.v1 = (float*)(q + 2 * ((acc * 4 + 255) & ~255LL));
-    const size_t shm = (size_t)(C + 1) * sizeof(int32_t);
+    store.v1 = store.v0 + acc;
+    char* wp = q + ((store_bytes + 255) & ~(size_t)255);
+    auto wtake = [&](size_t nbytes) {
+        char* r = wp;
+        wp += (nbytes + 255) & ~(size_t)255;
+        return r;
+    };
+    P1Work w;
+    w.kpfx = (int64_t*)wtake((size_t)(S + 1) * 8);
+    w.leafmean = (float*)wtake((size_t)S * C * 4);
+    w.thr = (float*)wtake((size_t)S * 4);
+    w.mcount = (int64_t*)wtake((size_t)Hn * 8);
+    w.bcount = (int64_t*)wtake((size_t)Hn * 8);
+    w.mdst = (int64_t*)wtake((size_t)mcap * 8);
+    w.mpt = (int32_t*)wtake((size_t)mcap * 4);
+    w.mnode = (int32_t*)wtake((size_t)mcap * 4);
+    w.big = (int64_t*)wtake((size_t)bcap * 8);
+    w.mcap = mcap;
+    w.bcap = bcap;
+    if ((size_t)(wp - q) > ctx->scr_size[SCR_P1_STORE])
+        return lt_fail(ctx, LT_ENOMEM, "lt_sample_pass1: work layout overflow");
+    LT_CUDA(ctx, cudaMemsetAsync(w.mcount, 0, (size_t)Hn * 8, ctx->stream));
+    LT_CUDA(ctx, cudaMemsetAsync(w.bcount, 0, (size_t)Hn * 8, ctx->stream));
+    const int nsm = ctx->num_sms;
+    const float dmin2 = d_min * d_min;
+    auto grid_for = [&](int64_t items, int threads) {
+        return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + threads - 1) / threads, 32 * (int64_t)nsm));
+    };
+    k_p1_draws<<<grid_for((int64_t)S * NF, 256), 256, 0, ctx->stream>>>(*f, seed, pl, store, ctx->d_status);
+    LT_LAUNCH_CHECK(ctx, "k_p1_draws");
+    k_p1_kpfx<<<1, 1024, 0, ctx->stream>>>(*f, pl, w.kpfx);
+    LT_LAUNCH_CHECK(ctx, "k_p1_kpfx");
+    k_p1_initial<<<16 * nsm, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, pl, store, w.kpfx);
+    LT_LAUNCH_CHECK(ctx, "k_p1_initial");
+    k_p1_leafmean<<<grid_for((int64_t)S * C, 256), 256, 0, ctx->stream>>>(*f, pl, store, w.leafmean);
+    LT_LAUNCH_CHECK(ctx, "k_p1_leafmean");
+    k_p1_thr<<<S, 256, 0, ctx->stream>>>(*f, w.leafmean, tau, w.thr);
+    LT_LAUNCH_CHECK(ctx, "k_p1_thr");
+    std::vector<int32_t> loff(f->H + 2, 0);
+    if (f->H > 0)
+        LT_CUDA(ctx, cudaMemcpyAsync(loff.data(), f->level_off, (f->H + 2) * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int h = 1; h <= f->H; ++h) {
+        const int64_t npairs = (int64_t)S * (loff[h + 1] - loff[h]);
+        if (npairs == 0) continue;
+        k_p1_setup<<<grid_for(npairs, 128), 128, 0, ctx->stream>>>(*f, pl, store, w, h, ctx->d_status);
+        LT_LAUNCH_CHECK(ctx, "k_p1_setup");
+        k_p1_setup_big<<<4 * nsm, 256, 0, ctx->stream>>>(*f, pl, store, w, h, ctx->d_status);
+        LT_LAUNCH_CHECK(ctx, "k_p1_setup_big");
+        k_p1_rays<<<16 * nsm, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, store, w, h);
+        LT_LAUNCH_CHECK(ctx, "k_p1_rays");
+        k_p1_decide<<<grid_for(npairs, 128), 128, 0, ctx->stream>>>(*f, pl, store, w, h);
+        LT_LAUNCH_CHECK(ctx, "k_p1_decide");
+        k_p1_decide_big<<<4 * nsm, 256, 0, ctx->stream>>>(*f, pl, store, w, h);
+        LT_LAUNCH_CHECK(ctx, "k_p1_decide_big");
+    }
+    const size_t shm = (size_t)C * 4;
     if (shm > 16 * 1024)
-        LT_CUDA(ctx, cudaFuncSetAttribute(k_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_pass1<<<S, kP1Threads, shm, ctx->stream>>>(*f, ctx->grid, rate1, tau, d_min * d_min, seed, pl, store, *smp,
-                                                 ctx->d_status);
-    LT_LAUNCH_CHECK(ctx, "k_pass1");
+        LT_CUDA(ctx, cudaFuncSetAttribute(k_p1_output, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_p1_output<<<S, kP1Threads, shm, ctx->stream>>>(*f, pl, store, *smp, ctx->d_status);
+    LT_LAUNCH_CHECK(ctx, "k_p1_output");
     // memory stays referenced by the stream: the host vectors were consumed by the
     // synchronous copy above and the async upload below must finish before return
     LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
