@@ -221,6 +221,10 @@ def run_ours(args):
     for i in range(args.warmup):
         frame(i)
     lt.lt_sync(ctx)
+    graph = R.capture()  # the batched form: the whole frame as one CUDA graph
+    for i in range(args.warmup):
+        R.render_graph(seed0 + 100 + i, sync=False)
+    lt.lt_sync(ctx)
 
     if world > 1:
         dist.barrier()
@@ -228,16 +232,16 @@ def run_ours(args):
     launches0 = lt.lt_launch_count(ctx)
     clocks = ClockSampler(local)
     per = []
-    stage_ms = np.zeros(5)
     for k in range(args.steps):
         flush.zero_()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-        frame(1000 + k, evs)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.render_graph(seed0 + 1000 + k, sync=False)
+        b.record()
         torch.cuda.synchronize()
-        per.append(evs[0].elapsed_time(evs[5]))
-        stage_ms += np.array([evs[j].elapsed_time(evs[j + 1]) for j in range(5)])
+        per.append(a.elapsed_time(b))
     torch.cuda.synchronize()
-    clk = clocks.stop()
     launches = lt.lt_launch_count(ctx) - launches0
     lt.lt_sync(ctx)
     total_ms = float(sum(per))
@@ -246,8 +250,25 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         dist.barrier()
-    stage_ms /= args.steps
     ms_frame = total_ms / (args.steps * world)
+    img_graph = R.img.clone()
+
+    # the plain form (the same calls one by one, with the two size read-backs),
+    # with events between the stages for the breakdown
+    plain = []
+    stage_ms = np.zeros(5)
+    for k in range(args.steps):
+        flush.zero_()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        frame(1000 + k, evs)
+        torch.cuda.synchronize()
+        plain.append(evs[0].elapsed_time(evs[5]))
+        stage_ms += np.array([evs[j].elapsed_time(evs[j + 1]) for j in range(5)])
+    clk = clocks.stop()
+    lt.lt_sync(ctx)
+    stage_ms /= args.steps
+    plain_ms = statistics.mean(plain)
+    same_as_graph = bool(torch.equal(R.img, img_graph))
 
     # quality: the last frame against the brute-force column sum over all VPLs
     img = R.img.clone()
@@ -278,7 +299,7 @@ def run_ours(args):
         R.pts.copy_(pts_h, non_blocking=True)
         R.vpls.copy_(vpl_h, non_blocking=True)
         R.pts_s.copy_(lt.lt_permute_points(ctx, R.pts, R.row_perm))
-        frame(5000 + k)
+        R.render_graph(seed0 + 5000 + k, sync=False)
         img_h.copy_(R.img, non_blocking=True)
         b.record()
         torch.cuda.synchronize()
@@ -299,6 +320,10 @@ def run_ours(args):
                             l2="flushed (256 MB write) between timed frames", global_cut=int(R.frame.C),
                             rel_rmse_vs_bruteforce=round(rel, 5), rays_per_pixel=round(rays_per_px, 2),
                             bruteforce_gpu_ms=round(bf_ms, 3), speedup_vs_bruteforce=round(bf_ms / ms_frame, 2),
+                            form="batched: the frame as one captured CUDA graph, "
+                                 f"{graph.kernels} kernels per replay",
+                            plain_form_ms=round(plain_ms, 4), speedup_vs_plain_form=round(plain_ms / ms_frame, 3),
+                            plain_equals_graph_bitwise=same_as_graph,
                             setup_ms=round(setup_ms, 1),
                             stage_ms=dict(zip(["pass1", "pass2", "eval", "complete", "render"],
                                               [round(x, 4) for x in stage_ms.tolist()]))),

@@ -219,6 +219,44 @@ lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int
 lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
                     const float* w, const int32_t* row_perm, float* img);
 
+/* ---- The whole frame (Sec. 3 steps 3-5) ----------------------------------- */
+/* Parameters of one frame. */
+typedef struct {
+    float rate1;          /* pass-1 density (rows per cut node, see lt_sample_pass1) */
+    float tau;            /* coarsening threshold of Eq. 2 */
+    float d_min;          /* distance clamp of the geometry term */
+    float rate;           /* total sampling rate of a slice (pass 1 + pass 2) */
+    int32_t als_iters;    /* ALS sweeps */
+    float lam_rel;        /* ALS ridge, relative to trace(G)/r */
+    const float* weights; /* pass-2 column weights [S][C]; NULL = the pass-1 estimate g (Sec. 5) */
+} lt_params;
+
+/* One frame as a sequence of launches on the context's stream: lt_sample_pass1,
+ * lt_sample_pass2, lt_eval_entries, lt_complete (rank uv->r) and lt_render with
+ * w = NULL, all with `seed`.  It reads two setup-dependent sizes back from the
+ * device, so it synchronises the stream twice. */
+lt_status lt_render_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed,
+                          lt_samples* smp, lt_factors* uv, const int32_t* row_perm, float* img);
+
+/* A frame captured once as a CUDA graph and replayed for any seed, with no host
+ * synchronisation and one graph launch per frame.  The paper has no counterpart
+ * (it is the batched form of the same steps).  Capture runs the frame once
+ * unrecorded with seed 0 (this writes smp, uv and img), then records it; the sizes
+ * read back by the unrecorded run are fixed in the graph.  The graph keeps every
+ * pointer it was given (frame, samples, factors, row_perm, img, weights) and the
+ * context's scene and scratch: keep them alive and unchanged in size, do not
+ * re-upload the scene, and destroy the graph before the context.  Launches go to
+ * the context's stream; a replay writes the same buffers as lt_render_frame with
+ * the same seed.  Errors: LT_EINVAL for bad arguments, LT_ECUDA if capture or
+ * instantiation fails; device errors of a replay are latched as usual. */
+typedef struct lt_graph lt_graph;
+lt_status lt_frame_graph_capture(lt_ctx* ctx, const lt_frame* f, const lt_params* p, lt_samples* smp,
+                                 lt_factors* uv, const int32_t* row_perm, float* img, lt_graph** g);
+lt_status lt_frame_graph_launch(lt_graph* g, uint64_t seed);
+/* Kernels recorded in the graph (instrumentation). */
+int64_t lt_frame_graph_kernels(const lt_graph* g);
+lt_status lt_frame_graph_destroy(lt_graph* g);
+
 #ifdef __cplusplus
 }
 #endif

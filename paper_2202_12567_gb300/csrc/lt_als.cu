@@ -142,8 +142,9 @@ __global__ void k_line_prefix(const lt_samples smp, int S, int64_t* pfx) {
     if (threadIdx.x == 0) pfx[S] = carry;
 }
 
-__global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int r, uint64_t seed, float* __restrict__ V) {
+__global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int r, SeedRef sr, float* __restrict__ V) {
     const int s = blockIdx.y;
+    const uint64_t seed = sr.get();
     const int ns = smp.ncol[s];
     const float amp = sqrtf(fmaxf(om.mu[s], 0.f) / (float)r);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns * r; i += gridDim.x * blockDim.x) {
@@ -702,11 +703,15 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         return lt_fail(ctx, LT_EINVAL, "lt_complete: bad arguments");
     cudaSetDevice(ctx->device);
     const int S = f->S, C = f->C;
-    std::vector<int64_t> off(S + 1);
-    LT_CUDA(ctx, cudaMemcpyAsync(off.data(), smp->off, (S + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                                 ctx->stream));
-    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const int64_t E = off[S];
+    // The sampling capacity sizes the scratch; a captured frame reuses the recorded value.
+    int64_t E = 0;
+    if (ctx->use_plan) {
+        E = ctx->plan.entries;
+    } else {
+        LT_CUDA(ctx, cudaMemcpyAsync(&E, smp->off + S, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->plan.entries = E;
+    }
     const int64_t mr = std::max(f->max_rows, 1);
     Omega om;
     om.bm_stride = mr * ((C + 31) / 32);
@@ -742,7 +747,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     k_line_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, S, om.line_pfx);
     LT_LAUNCH_CHECK(ctx, "k_line_prefix");
     const int r = uv->r;
-    k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, r, seed, uv->V);
+    k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, r, seed_ref(ctx, seed), uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
     // CTAs per slice: about two per SM over the whole grid
     const int P = std::max(1, (2 * ctx->num_sms + S - 1) / S);

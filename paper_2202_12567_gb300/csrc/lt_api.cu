@@ -39,9 +39,17 @@ void* lt_scratch(lt_ctx* ctx, int slot, size_t bytes, lt_status* st) {
     *st = LT_OK;
     if (bytes == 0) bytes = 256;
     if (ctx->scr_size[slot] >= bytes) return ctx->scr[slot];
+    if (ctx->use_plan) {  // a captured frame must find the scratch its warm run sized
+        *st = lt_fail(ctx, LT_EINVAL, "scratch growth while a frame is being captured");
+        return nullptr;
+    }
     if (ctx->scr[slot]) {
-        cudaStreamSynchronize(ctx->stream);
-        cudaFree(ctx->scr[slot]);
+        if (ctx->graphs > 0) {
+            ctx->retired.push_back(ctx->scr[slot]);  // a live graph may still use it
+        } else {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->scr[slot]);
+        }
         ctx->scr[slot] = nullptr;
         ctx->scr_size[slot] = 0;
     }
@@ -82,10 +90,12 @@ extern "C" lt_status lt_create(lt_ctx** out, int device, void* stream) {
 
 extern "C" lt_status lt_destroy(lt_ctx* ctx) {
     if (!ctx) return LT_EINVAL;
+    if (ctx->graphs > 0) return lt_fail(ctx, LT_EINVAL, "lt_destroy: destroy the context's frame graphs first");
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     for (int i = 0; i < SCR_NSLOTS; ++i)
         if (ctx->scr[i]) cudaFree(ctx->scr[i]);
+    for (void* q : ctx->retired) cudaFree(q);
     cudaFree(ctx->d_boxes);
     cudaFree(ctx->d_cell_off);
     cudaFree(ctx->d_cell_box);
@@ -125,6 +135,8 @@ extern "C" lt_status lt_sync(lt_ctx* ctx) {
 extern "C" lt_status lt_scene_upload(lt_ctx* ctx, const float* boxes, int64_t nb, int32_t grid_res) {
     if (!ctx || nb < 0 || (nb > 0 && !boxes) || grid_res < 0 || grid_res > 128 || nb > (1 << 24))
         return lt_fail(ctx, LT_EINVAL, "lt_scene_upload: bad arguments");
+    if (ctx->graphs > 0)
+        return lt_fail(ctx, LT_EINVAL, "lt_scene_upload: live frame graphs reference the current scene");
     cudaSetDevice(ctx->device);
     std::vector<float> hb((size_t)nb * 6);
     if (nb) {

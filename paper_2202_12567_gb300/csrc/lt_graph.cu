@@ -1,0 +1,141 @@
+// The whole frame: the plain sequence of launches and its captured CUDA graph.
+//
+// A frame is Sec. 3 steps 3-5: pass 1 with coarsening (Sec. 4), pass 2 (Sec. 5),
+// evaluation of the new entries, completion and the factorised render.  Every call
+// of the sequence is sync-free except two read-backs of sizes that depend on the
+// setup only (pass-1 row slots and forest levels; the sampling capacity).  The
+// graph form records them in a warm run, then captures the frame on a private
+// stream with those sizes fixed and the seed read from a device word, so one
+// instantiated graph replays any seed with a single launch.
+#include "lt_internal.cuh"
+
+using namespace ltk;
+
+struct lt_graph {
+    lt_ctx* ctx = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t* d_seed = nullptr;
+    int64_t kernels = 0;
+};
+
+namespace {
+
+__global__ void k_set_seed(uint64_t* dst, uint64_t seed) { *dst = seed; }
+
+bool params_ok(const lt_params* p) {
+    return p && p->rate1 >= 0.f && p->tau >= 0.f && p->d_min >= 0.f && p->rate >= 0.f && p->als_iters >= 0 &&
+           p->lam_rel >= 0.f;
+}
+
+lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed, lt_samples* smp,
+                    lt_factors* uv, const int32_t* row_perm, float* img) {
+    lt_status st = lt_sample_pass1(ctx, f, p->rate1, p->tau, p->d_min, seed, smp);
+    if (st != LT_OK) return st;
+    st = lt_sample_pass2(ctx, f, p->weights, p->rate, seed, smp);
+    if (st != LT_OK) return st;
+    st = lt_eval_entries(ctx, f, p->d_min, smp);
+    if (st != LT_OK) return st;
+    st = lt_complete(ctx, f, smp, p->als_iters, p->lam_rel, seed, uv);
+    if (st != LT_OK) return st;
+    return lt_render(ctx, f, smp, uv, nullptr, row_perm, img);
+}
+
+}  // namespace
+
+extern "C" lt_status lt_render_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed,
+                                     lt_samples* smp, lt_factors* uv, const int32_t* row_perm, float* img) {
+    if (!ctx || !f || !params_ok(p) || !smp || !uv || !row_perm || !img)
+        return lt_fail(ctx, LT_EINVAL, "lt_render_frame: bad arguments");
+    return run_frame(ctx, f, p, seed, smp, uv, row_perm, img);
+}
+
+extern "C" lt_status lt_frame_graph_capture(lt_ctx* ctx, const lt_frame* f, const lt_params* p, lt_samples* smp,
+                                            lt_factors* uv, const int32_t* row_perm, float* img, lt_graph** out) {
+    if (!ctx || !f || !params_ok(p) || !smp || !uv || !row_perm || !img || !out)
+        return lt_fail(ctx, LT_EINVAL, "lt_frame_graph_capture: bad arguments");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    // warm run: records the setup-dependent sizes and grows the scratch to them
+    lt_status st = run_frame(ctx, f, p, 0, smp, uv, row_perm, img);
+    if (st != LT_OK) return st;
+    st = lt_sync(ctx);
+    if (st != LT_OK) return st;
+    lt_graph* g = new lt_graph();
+    g->ctx = ctx;
+    cudaError_t e = cudaMalloc(&g->d_seed, sizeof(uint64_t));
+    if (e != cudaSuccess) {
+        delete g;
+        return lt_cuda_check(ctx, e, "cudaMalloc(seed)");
+    }
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_seed);
+        delete g;
+        return lt_cuda_check(ctx, e, "cudaStreamCreateWithFlags");
+    }
+    cudaStream_t orig = ctx->stream;
+    const int64_t n0 = ctx->launches;
+    ctx->stream = cap;
+    ctx->use_plan = true;
+    ctx->seed_dev = g->d_seed;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        st = run_frame(ctx, f, p, 0, smp, uv, row_perm, img);
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (st == LT_OK && e2 != cudaSuccess) st = lt_cuda_check(ctx, e2, "cudaStreamEndCapture");
+    } else {
+        st = lt_cuda_check(ctx, e, "cudaStreamBeginCapture");
+    }
+    ctx->stream = orig;
+    ctx->use_plan = false;
+    ctx->seed_dev = nullptr;
+    g->kernels = ctx->launches - n0;
+    ctx->launches = n0;
+    cudaStreamDestroy(cap);
+    if (st == LT_OK) {
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (e != cudaSuccess) st = lt_cuda_check(ctx, e, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != LT_OK) {
+        cudaGetLastError();
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        cudaFree(g->d_seed);
+        delete g;
+        return st;
+    }
+    ctx->graphs++;
+    *out = g;
+    return LT_OK;
+}
+
+extern "C" lt_status lt_frame_graph_launch(lt_graph* g, uint64_t seed) {
+    if (!g || !g->ctx || !g->exec) return LT_EINVAL;
+    lt_ctx* ctx = g->ctx;
+    cudaSetDevice(ctx->device);
+    k_set_seed<<<1, 1, 0, ctx->stream>>>(g->d_seed, seed);
+    LT_LAUNCH_CHECK(ctx, "k_set_seed");
+    LT_CUDA(ctx, cudaGraphLaunch(g->exec, ctx->stream));
+    ctx->launches += g->kernels;
+    return LT_OK;
+}
+
+extern "C" int64_t lt_frame_graph_kernels(const lt_graph* g) { return g ? g->kernels : 0; }
+
+extern "C" lt_status lt_frame_graph_destroy(lt_graph* g) {
+    if (!g) return LT_EINVAL;
+    lt_ctx* ctx = g->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    cudaFree(g->d_seed);
+    ctx->graphs--;
+    if (ctx->graphs == 0) {
+        for (void* q : ctx->retired) cudaFree(q);
+        ctx->retired.clear();
+    }
+    delete g;
+    return LT_OK;
+}

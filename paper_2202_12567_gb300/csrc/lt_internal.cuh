@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/lt.h"
 
@@ -19,6 +20,14 @@ constexpr float kTMin = 1e-4f;
 constexpr float kTMax = 1.0f - 1e-4f;
 constexpr float kInvPi = 0.318309886183790672f;
 constexpr uint32_t kTagPass1 = 1, kTagPass2 = 2, kTagAlsInit = 3;
+
+// The seed of a frame: passed by value, or read from a device word so that one
+// captured graph replays every seed.
+struct SeedRef {
+    uint64_t value;
+    const uint64_t* dev;
+    __device__ __forceinline__ uint64_t get() const { return dev ? *dev : value; }
+};
 
 // ----------------------------------------------------------------- Philox4x32-10
 struct U4 {
@@ -370,7 +379,21 @@ struct lt_ctx {
     size_t scr_size[SCR_NSLOTS] = {};
     int num_sms = 0;
     int64_t launches = 0;   // kernels launched through this context
+    // Sizes that the frame calls read back from the device.  They depend on the
+    // frame's setup (cut, forest, slices, sampling capacity), never on the seed, so a
+    // replayed frame (graph capture) takes them from here instead of synchronising.
+    struct Plan {
+        int64_t p1_total = 0;              // pass-1 row slots of all slices
+        std::vector<int32_t> level_off;    // forest level offsets [H + 2]
+        int64_t entries = 0;               // sampling capacity off[S]
+    } plan;
+    bool use_plan = false;                 // set while a frame is captured
+    const uint64_t* seed_dev = nullptr;    // device seed word of the graph being captured
+    std::vector<void*> retired;            // scratch that live graphs may still reference
+    int graphs = 0;                        // graphs alive on this context
 };
+
+inline ltk::SeedRef seed_ref(const lt_ctx* ctx, uint64_t seed) { return ltk::SeedRef{seed, ctx->seed_dev}; }
 
 // Helpers implemented in lt_api.cu.
 lt_status lt_fail(lt_ctx* ctx, lt_status code, const std::string& msg);

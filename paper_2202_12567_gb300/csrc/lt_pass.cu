@@ -131,8 +131,9 @@ struct P1Work {
 };
 
 // -- draws of the cut nodes and state of every forest node
-__global__ void k_p1_draws(lt_frame F, uint64_t seed, P1Plan pl, P1Store st, int32_t* status) {
+__global__ void k_p1_draws(lt_frame F, SeedRef sr, P1Plan pl, P1Store st, int32_t* status) {
     const int C = F.C, NF = 2 * C - 1;
+    const uint64_t seed = sr.get();
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)F.S * NF;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int s = (int)(idx / NF), x = (int)(idx % NF);
@@ -173,6 +174,20 @@ __global__ void k_p1_draws(lt_frame F, uint64_t seed, P1Plan pl, P1Store st, int
         }
         cnt[x] = got;
         state[x] = ms > 0 ? kStAlive : kStNot;
+    }
+}
+
+// -- first row slot of every slice: exclusive prefix of the per-slice totals
+__global__ void k_p1_base(int S, P1Plan pl) {
+    __shared__ int64_t ws[32];
+    int64_t carry = 0;
+    for (int c0 = 0; c0 < S; c0 += blockDim.x) {
+        const int s = c0 + threadIdx.x;
+        const int64_t x = s < S ? pl.total[s] : 0;
+        int64_t tot;
+        const int64_t pre = block_exclusive_scan<int64_t>(x, ws, &tot);
+        if (s < S) pl.base[s] = carry + pre;
+        carry += tot;
     }
 }
 
@@ -640,7 +655,7 @@ constexpr int kHashSize = 2 * kP2Threads;
 constexpr uint32_t kEmpty = 0xffffffffu;
 
 __global__ void __launch_bounds__(kP2Threads) k_pass2(lt_frame F, const float* __restrict__ weights, float rate,
-                                                      uint64_t seed, lt_samples smp, uint32_t* bitmap_all,
+                                                      SeedRef sr, lt_samples smp, uint32_t* bitmap_all,
                                                       int64_t bitmap_stride, int32_t* status) {
     extern __shared__ unsigned long long cdf[];  // [C]
     __shared__ uint32_t hkey[kHashSize];
@@ -653,6 +668,7 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(lt_frame F, const float* _
     const int ms = F.slice_off[s + 1] - F.slice_off[s];
     const int ns = smp.ncol[s];
     const int n1 = smp.n1[s];
+    const uint64_t seed = sr.get();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (ms == 0 || ns == 0) {
         if (threadIdx.x == 0) smp.cnt[s] = n1;
@@ -879,15 +895,20 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
         return lt_fail(ctx, LT_ENOMEM, "lt_sample_pass1: plan layout overflow");
     k_pass1_plan<<<S, kP1Threads, 0, ctx->stream>>>(*f, rate1, pl);
     LT_LAUNCH_CHECK(ctx, "k_pass1_plan");
-    std::vector<int64_t> tot(S), basev(S);
-    LT_CUDA(ctx, cudaMemcpyAsync(tot.data(), pl.total, S * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    k_p1_base<<<1, 1024, 0, ctx->stream>>>(S, pl);
+    LT_LAUNCH_CHECK(ctx, "k_p1_base");
+    // The row-slot total sizes the scratch below; it follows from the setup alone
+    // (cut, forest, slices, rate1), so a captured frame reuses the recorded value.
     int64_t acc = 0;
-    for (int s = 0; s < S; ++s) {
-        basev[s] = acc;
-        acc += tot[s];
+    if (ctx->use_plan) {
+        acc = ctx->plan.p1_total;
+    } else {
+        std::vector<int64_t> tot(S);
+        LT_CUDA(ctx, cudaMemcpyAsync(tot.data(), pl.total, S * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        for (int s = 0; s < S; ++s) acc += tot[s];
+        ctx->plan.p1_total = acc;
     }
-    LT_CUDA(ctx, cudaMemcpyAsync(pl.base, basev.data(), S * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
     // storage: rows, then v0 and v1 back to back (a flat value index addresses both);
     // then the work arrays of the flat kernels
     const int Hn = f->H + 2;
@@ -929,7 +950,8 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     auto grid_for = [&](int64_t items, int threads) {
         return (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + threads - 1) / threads, 32 * (int64_t)nsm));
     };
-    k_p1_draws<<<grid_for((int64_t)S * NF, 256), 256, 0, ctx->stream>>>(*f, seed, pl, store, ctx->d_status);
+    k_p1_draws<<<grid_for((int64_t)S * NF, 256), 256, 0, ctx->stream>>>(*f, seed_ref(ctx, seed), pl, store,
+                                                                        ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_p1_draws");
     k_p1_kpfx<<<1, 1024, 0, ctx->stream>>>(*f, pl, w.kpfx);
     LT_LAUNCH_CHECK(ctx, "k_p1_kpfx");
@@ -940,9 +962,17 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     k_p1_thr<<<S, 256, 0, ctx->stream>>>(*f, w.leafmean, tau, w.thr);
     LT_LAUNCH_CHECK(ctx, "k_p1_thr");
     std::vector<int32_t> loff(f->H + 2, 0);
-    if (f->H > 0)
-        LT_CUDA(ctx, cudaMemcpyAsync(loff.data(), f->level_off, (f->H + 2) * 4, cudaMemcpyDeviceToHost, ctx->stream));
-    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->use_plan) {
+        if ((int)ctx->plan.level_off.size() != f->H + 2)
+            return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1: recorded frame plan does not match the forest");
+        loff = ctx->plan.level_off;
+    } else {
+        if (f->H > 0)
+            LT_CUDA(ctx, cudaMemcpyAsync(loff.data(), f->level_off, (f->H + 2) * 4, cudaMemcpyDeviceToHost,
+                                         ctx->stream));
+        LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->plan.level_off = loff;
+    }
     for (int h = 1; h <= f->H; ++h) {
         const int64_t npairs = (int64_t)S * (loff[h + 1] - loff[h]);
         if (npairs == 0) continue;
@@ -962,9 +992,6 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
         LT_CUDA(ctx, cudaFuncSetAttribute(k_p1_output, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     k_p1_output<<<S, kP1Threads, shm, ctx->stream>>>(*f, pl, store, *smp, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_p1_output");
-    // memory stays referenced by the stream: the host vectors were consumed by the
-    // synchronous copy above and the async upload below must finish before return
-    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return LT_OK;
 }
 
@@ -981,7 +1008,8 @@ extern "C" lt_status lt_sample_pass2(lt_ctx* ctx, const lt_frame* f, const float
     const size_t shm = (size_t)C * 8;
     if (shm > 16 * 1024)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_pass2<<<S, kP2Threads, shm, ctx->stream>>>(*f, weights, rate, seed, *smp, bm, stride, ctx->d_status);
+    k_pass2<<<S, kP2Threads, shm, ctx->stream>>>(*f, weights, rate, seed_ref(ctx, seed), *smp, bm, stride,
+                                                 ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_pass2");
     return LT_OK;
 }

@@ -55,6 +55,11 @@ class lt_factors(ctypes.Structure):
     _fields_ = [("r", _i32), ("U", _p), ("V", _p)]
 
 
+class lt_params(ctypes.Structure):
+    _fields_ = [("rate1", _f32), ("tau", _f32), ("d_min", _f32), ("rate", _f32), ("als_iters", _i32),
+                ("lam_rel", _f32), ("weights", _p)]
+
+
 _SIGS = {
     "lt_status_str": (ctypes.c_char_p, [_i32]),
     "lt_last_error": (ctypes.c_char_p, [_p]),
@@ -83,6 +88,14 @@ _SIGS = {
                            ctypes.POINTER(lt_factors)]),
     "lt_render": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p,
                          _p, _p]),
+    "lt_render_frame": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_params), _u64,
+                               ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p, _p]),
+    "lt_frame_graph_capture": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_params),
+                                      ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p, _p,
+                                      ctypes.POINTER(_p)]),
+    "lt_frame_graph_launch": (_i32, [_p, _u64]),
+    "lt_frame_graph_kernels": (_i64, [_p]),
+    "lt_frame_graph_destroy": (_i32, [_p]),
 }
 
 EXPORTED = sorted(_SIGS)
@@ -368,3 +381,59 @@ def lt_complete(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, la
 def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, img, w=None):
     ctx._check("lt_render", ctx.lib.lt_render(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
                                               ctypes.byref(uv.struct()), _ptr(w), _ptr(row_perm), _ptr(img)))
+
+
+def params(cfg: dict, weights=None) -> lt_params:
+    """lt_params of a configuration dict (rate1, tau, d_min, rate, als_iters, lam_rel)."""
+    return lt_params(cfg["rate1"], cfg["tau"], cfg["d_min"], cfg["rate"], cfg["als_iters"], cfg["lam_rel"],
+                     _ptr(weights))
+
+
+def lt_render_frame(ctx: Context, frame: Frame, prm: lt_params, seed, smp: Samples, uv: Factors, row_perm, img):
+    ctx._check("lt_render_frame", ctx.lib.lt_render_frame(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(prm),
+                                                          seed, ctypes.byref(smp.struct()), ctypes.byref(uv.struct()),
+                                                          _ptr(row_perm), _ptr(img)))
+
+
+class Graph:
+    """A captured frame (lt_graph); holds every object whose memory the graph uses."""
+
+    def __init__(self, ctx: Context, frame: Frame, prm: lt_params, smp: Samples, uv: Factors, row_perm, img,
+                 keep=()):
+        self.ctx = ctx
+        self._keep = (frame, prm, smp, uv, row_perm, img, *keep)
+        h = _p()
+        ctx._check("lt_frame_graph_capture",
+                   ctx.lib.lt_frame_graph_capture(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(prm),
+                                                  ctypes.byref(smp.struct()), ctypes.byref(uv.struct()),
+                                                  _ptr(row_perm), _ptr(img), ctypes.byref(h)))
+        self.h = h
+        self.kernels = int(ctx.lib.lt_frame_graph_kernels(h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.lt_frame_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lt_frame_graph_capture(ctx: Context, frame: Frame, prm: lt_params, smp: Samples, uv: Factors, row_perm, img,
+                           keep=()) -> Graph:
+    return Graph(ctx, frame, prm, smp, uv, row_perm, img, keep)
+
+
+def lt_frame_graph_launch(g: Graph, seed):
+    g.ctx._check("lt_frame_graph_launch", g.ctx.lib.lt_frame_graph_launch(g.h, seed))
+
+
+def lt_frame_graph_kernels(g: Graph) -> int:
+    return int(g.ctx.lib.lt_frame_graph_kernels(g.h))
+
+
+def lt_frame_graph_destroy(g: Graph):
+    g.close()

@@ -97,6 +97,30 @@ class Renderer:
             lt.lt_sync(self.ctx)
         return self.img
 
+    def render_frame(self, seed=None, weights=None, sync=True):
+        """The same frame through the single C entry point lt_render_frame."""
+        seed = self.cfg["frame_seed"] if seed is None else seed
+        self._prm = lt.params(self.cfg, weights)
+        lt.lt_render_frame(self.ctx, self.frame, self._prm, seed, self.smp, self.uv, self.row_perm, self.img)
+        if sync:
+            lt.lt_sync(self.ctx)
+        return self.img
+
+    def capture(self, weights=None):
+        """Capture the frame as a CUDA graph (lt_frame_graph_capture); replay with render_graph."""
+        if getattr(self, "graph", None) is not None:
+            self.graph.close()
+        self.graph = lt.lt_frame_graph_capture(self.ctx, self.frame, lt.params(self.cfg, weights), self.smp, self.uv,
+                                               self.row_perm, self.img, keep=(weights,))
+        return self.graph
+
+    def render_graph(self, seed=None, sync=True):
+        seed = self.cfg["frame_seed"] if seed is None else seed
+        lt.lt_frame_graph_launch(self.graph, seed)
+        if sync:
+            lt.lt_sync(self.ctx)
+        return self.img
+
     def bruteforce(self, out=None):
         return lt.lt_bruteforce(self.ctx, self.pts, self.vpls, self.cfg["d_min"], out)
 
