@@ -37,29 +37,51 @@ struct Omega {
     uint32_t* wc;       // per word of bt: set bits before it in its column
     int64_t bm_stride, bt_stride;
     int64_t* line_pfx;  // [S + 1] prefix of n'_s (V-step lines)
+    int32_t* rord;      // [m]          rows of each slice by decreasing entry count
+    int32_t* cord;      // [S][C]       columns of each slice by decreasing entry count
+    int32_t* rcls;      // [S][16]      per group-size class g: first sorted row, first warp task
+    int32_t* ccls;      // [S][16]      the same for the columns
 };
 
-__global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omega om, int32_t* status) {
-    __shared__ int32_t ws[32];
+// Group-size classes of a line: class g gives a line of L entries G = 2^g lanes, so
+// that a lane takes at most about kLaneEntries of them (g = 0..5).
+constexpr int kLaneEntries = 96, kClasses = 6;
+
+__host__ __device__ inline int line_class(int len) {
+    int g = 0;
+    while (g < kClasses - 1 && len > (kLaneEntries << g)) ++g;
+    return g;
+}
+
+// Omega build in five passes over the whole GPU (slice = blockIdx.y):
+//  1. clear the used words of both bitmaps;  2. set the bit of every entry and sum
+//  the values (one partial per block, fixed order);  3. one warp per row (column):
+//  popcount of each bitmap word, warp scan into the per-word prefix, line count;
+//  4. one block per slice: exclusive scan of the line counts into row / column
+//  pointers, mean value;  5. one thread per entry: slot = pointer + bits before.
+__global__ void k_om_clear(lt_frame F, lt_samples smp, Omega om) {
+    const int s = blockIdx.y;
+    const int ms = F.slice_off[s + 1] - F.slice_off[s], ns = smp.ncol[s];
+    const int64_t nbm = (int64_t)ms * ((ns + 31) >> 5), nbt = (int64_t)ns * ((ms + 31) >> 5);
+    uint32_t* bm = om.bm + (int64_t)s * om.bm_stride;
+    uint32_t* bt = om.bt + (int64_t)s * om.bt_stride;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbm; i += (int64_t)gridDim.x * blockDim.x)
+        bm[i] = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbt; i += (int64_t)gridDim.x * blockDim.x)
+        bt[i] = 0u;
+}
+
+__global__ void k_om_bits(lt_frame F, lt_samples smp, Omega om, float* __restrict__ part, int32_t* status) {
     __shared__ float red[32];
-    const int s = blockIdx.x;
-    const int C = F.C;
-    const int row0 = F.slice_off[s];
-    const int ms = F.slice_off[s + 1] - row0;
-    const int ns = smp.ncol[s];
-    const int ne = smp.cnt[s];
+    const int s = blockIdx.y;
+    const int ms = F.slice_off[s + 1] - F.slice_off[s], ns = smp.ncol[s], ne = smp.cnt[s];
     const int W = (ns + 31) >> 5, WT = (ms + 31) >> 5;
     uint32_t* bm = om.bm + (int64_t)s * om.bm_stride;
     uint32_t* bt = om.bt + (int64_t)s * om.bt_stride;
-    uint32_t* wr = om.wr + (int64_t)s * om.bm_stride;
-    uint32_t* wc = om.wc + (int64_t)s * om.bt_stride;
     const uint32_t* key = smp.key + smp.off[s];
     const float* val = smp.val + smp.off[s];
-    for (int64_t i = threadIdx.x; i < (int64_t)ms * W; i += blockDim.x) bm[i] = 0u;
-    for (int64_t i = threadIdx.x; i < (int64_t)ns * WT; i += blockDim.x) bt[i] = 0u;
-    __syncthreads();
     float sum = 0.f;
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
         const uint32_t k = key[e];
         const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
         if (r >= ms || c >= ns) {
@@ -76,55 +98,169 @@ __global__ void __launch_bounds__(1024) k_omega(lt_frame F, lt_samples smp, Omeg
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        om.mu[s] = ne > 0 ? t / (float)ne : 0.f;
+        part[(int64_t)s * gridDim.x + blockIdx.x] = t;
     }
-    // per-word prefix counts and the row / column pointers
-    int32_t* rp = om.rp + row0 + s;
+}
+
+// one warp per line: word prefixes of one bitmap row, the line's count into cnt_out
+__device__ __forceinline__ void om_line_words(const uint32_t* __restrict__ bits, uint32_t* __restrict__ pfx,
+                                              int nw, int32_t* cnt_out) {
+    const int lane = threadIdx.x & 31;
     int carry = 0;
-    for (int r0 = 0; r0 < ms; r0 += blockDim.x) {
-        const int r = r0 + threadIdx.x;
-        int c = 0;
-        if (r < ms)
-            for (int w = 0; w < W; ++w) {
-                wr[(int64_t)r * W + w] = (uint32_t)c;
-                c += __popc(bm[(int64_t)r * W + w]);
-            }
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+        const int w = w0 + lane;
+        const int c = w < nw ? __popc(bits[w]) : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (w < nw) pfx[w] = (uint32_t)(carry + incl - c);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) *cnt_out = carry;
+}
+
+__global__ void k_om_lines(lt_frame F, lt_samples smp, Omega om) {
+    const int s = blockIdx.y;
+    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0, ns = smp.ncol[s];
+    const int W = (ns + 31) >> 5, WT = (ms + 31) >> 5;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int l = gw; l < ms + ns; l += nwarps) {
+        if (l < ms) {
+            const int64_t o = (int64_t)s * om.bm_stride + (int64_t)l * W;
+            om_line_words(om.bm + o, om.wr + o, W, om.rp + row0 + s + l + 1);
+        } else {
+            const int c = l - ms;
+            const int64_t o = (int64_t)s * om.bt_stride + (int64_t)c * WT;
+            om_line_words(om.bt + o, om.wc + o, WT, om.cp + (int64_t)s * (F.C + 1) + c + 1);
+        }
+    }
+}
+
+// in place: x[0] = 0, x[1..n] counts -> exclusive prefix x[0..n]
+__device__ void om_scan_counts(int32_t* x, int n, int32_t* ws) {
+    int carry = 0;
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const int c = i < n ? x[i + 1] : 0;
         int tot;
         const int pre = block_exclusive_scan<int>(c, ws, &tot);
-        if (r < ms) rp[r] = carry + pre;
+        if (i < n) x[i + 1] = carry + pre + c;
         carry += tot;
+        __syncthreads();
     }
-    if (threadIdx.x == 0) rp[ms] = carry;
-    int32_t* cp = om.cp + (int64_t)s * (C + 1);
-    carry = 0;
-    for (int c0 = 0; c0 < ns; c0 += blockDim.x) {
-        const int c = c0 + threadIdx.x;
-        int n = 0;
-        if (c < ns)
-            for (int w = 0; w < WT; ++w) {
-                wc[(int64_t)c * WT + w] = (uint32_t)n;
-                n += __popc(bt[(int64_t)c * WT + w]);
-            }
-        int tot;
-        const int pre = block_exclusive_scan<int>(n, ws, &tot);
-        if (c < ns) cp[c] = carry + pre;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) cp[ns] = carry;
+    if (threadIdx.x == 0) x[0] = 0;
+}
+
+// ord[0..n) = lines by decreasing count (ties by index), from the counts ptr[1..n]
+// before they are scanned; a block-wide bitonic sort in shared memory, or the
+// identity when n exceeds kOrdMax.
+constexpr int kOrdMax = 4096;
+
+// cls[0..7): first sorted line of each class, largest class first (cls[kClasses - 1 - g]
+// for class g) and cls[8..15): the first warp task of each, a class-g task covering
+// 32 / 2^g lines; cls[6] and cls[14] are the totals.
+__device__ void om_classes(const int32_t* __restrict__ cnt1, int n, const int32_t* __restrict__ ord, bool sorted,
+                           int32_t* __restrict__ cls) {
+    __shared__ int32_t num[kClasses];
+    if (threadIdx.x < kClasses) num[threadIdx.x] = 0;
     __syncthreads();
-    // an entry's slot: pointer + bits before its word + bits before it in its word
+    if (sorted)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&num[line_class(cnt1[ord[i]])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!sorted) num[0] = n;  // unsorted: every line on one lane
+        int line = 0, task = 0;
+        for (int k = 0; k < kClasses; ++k) {  // k-th run in the order = class kClasses - 1 - k
+            const int g = kClasses - 1 - k;
+            cls[k] = line;
+            cls[8 + k] = task;
+            line += num[g];
+            task += (num[g] + (32 >> g) - 1) / (32 >> g);
+        }
+        cls[kClasses] = line;
+        cls[8 + kClasses] = task;
+    }
+    __syncthreads();
+}
+
+__device__ void om_order(const int32_t* __restrict__ cnt1, int n, int32_t* __restrict__ ord,
+                         unsigned long long* key) {
+    if (n > kOrdMax) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) ord[i] = i;
+        __syncthreads();
+        return;
+    }
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        key[i] = i < n ? ((unsigned long long)(0xffffffffu - (uint32_t)cnt1[i]) << 32) | (uint32_t)i : ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= N; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = key[i], b = key[l];
+                    if ((a > b) == ((i & k) == 0)) {
+                        key[i] = b;
+                        key[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ord[i] = (int32_t)(key[i] & 0xffffffffu);
+    __syncthreads();
+}
+
+__global__ void k_om_scan(lt_frame F, lt_samples smp, Omega om, const float* __restrict__ part, int nparts) {
+    __shared__ int32_t ws[32];
+    __shared__ unsigned long long key[kOrdMax];
+    const int s = blockIdx.x;
+    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0, ns = smp.ncol[s], ne = smp.cnt[s];
+    om_order(om.rp + row0 + s + 1, ms, om.rord + row0, key);
+    om_classes(om.rp + row0 + s + 1, ms, om.rord + row0, ms <= kOrdMax, om.rcls + (int64_t)s * 16);
+    om_order(om.cp + (int64_t)s * (F.C + 1) + 1, ns, om.cord + (int64_t)s * F.C, key);
+    om_classes(om.cp + (int64_t)s * (F.C + 1) + 1, ns, om.cord + (int64_t)s * F.C, ns <= kOrdMax,
+               om.ccls + (int64_t)s * 16);
+    om_scan_counts(om.rp + row0 + s, ms, ws);
+    om_scan_counts(om.cp + (int64_t)s * (F.C + 1), ns, ws);
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int q = 0; q < nparts; ++q) t += part[(int64_t)s * nparts + q];
+        om.mu[s] = ne > 0 ? t / (float)ne : 0.f;
+    }
+}
+
+__global__ void k_om_scatter(lt_frame F, lt_samples smp, Omega om) {
+    const int s = blockIdx.y;
+    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0, ns = smp.ncol[s], ne = smp.cnt[s];
+    const int W = (ns + 31) >> 5, WT = (ms + 31) >> 5;
+    const uint32_t* bm = om.bm + (int64_t)s * om.bm_stride;
+    const uint32_t* bt = om.bt + (int64_t)s * om.bt_stride;
+    const uint32_t* wr = om.wr + (int64_t)s * om.bm_stride;
+    const uint32_t* wc = om.wc + (int64_t)s * om.bt_stride;
+    const int32_t* rp = om.rp + row0 + s;
+    const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
     const int64_t o = smp.off[s];
-    for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const uint32_t* key = smp.key + o;
+    const float* val = smp.val + o;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
         const uint32_t k = key[e];
         const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
         if (r >= ms || c >= ns) continue;
         const int64_t iw = (int64_t)r * W + (c >> 5), jw = (int64_t)c * WT + (r >> 5);
         const int pr = rp[r] + (int)wr[iw] + __popc(bm[iw] & ((1u << (c & 31)) - 1u));
         const int pc = cp[c] + (int)wc[jw] + __popc(bt[jw] & ((1u << (r & 31)) - 1u));
+        const float v = val[e];
         om.cidx[o + pr] = (uint16_t)c;
-        om.cval[o + pr] = val[e];
+        om.cval[o + pr] = v;
         om.ridx[o + pc] = (uint16_t)r;
-        om.rval[o + pc] = val[e];
+        om.rval[o + pc] = v;
     }
 }
 
@@ -467,117 +603,51 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
 // ---- rank <= 16: Gram on the tensor cores, then one thread per line ------------
 // The in-warp Cholesky of the line solve costs as many warp instructions as the
 // whole tensor-core Gram; a 16 x 16 Cholesky fits one thread's registers instead.
-// k_gram16 writes the lower triangle of every line's Gram and its right-hand side
-// element-major (Gg[e * stride + line], 136 + 16 values per line) into a buffer that
-// stays in L2; k_solve16 gives each line to one thread.
-constexpr int kGramVals = 136 + 16;
+// ---- Masked ALS, one thread per line (r <= 16) --------------------------------
+// A line is a row of U_s (U-step, its entries in CSR) or a column of V_s (V-step,
+// CSC).  The thread gathers the factor row x_j of each observed entry from the
+// slice's factor rows staged in shared memory and accumulates the lower triangle of
+// G = sum x_j x_j^T and b = sum a_j x_j in registers (RP(RP+1)/2 + RP values),
+// adds the ridge lam_rel tr(G)/r, factors G by Cholesky in float32 and solves.
+// Lines whose pivots fail the check go to a queue that a float64 pass solves.
+template <int RP>
+struct AlsQueue {
+    static constexpr int kVals = RP * (RP + 1) / 2 + RP;
+    int32_t* count;     // [1] lines queued by this half-step
+    int64_t* dst;       // [cap] output row offset (floats) of each queued line
+    float* gram;        // [cap][kVals] Gram lower triangle then right-hand side
+    int64_t cap;
+    int32_t* status;    // device status word (LT_ELIMIT when the queue overflows)
+};
 
-__global__ void __launch_bounds__(512, 1) k_gram16(lt_frame F, lt_samples smp, Omega om, int r, bool rows_side,
-                                                   const float* __restrict__ Fin, float* __restrict__ Gg,
-                                                   int64_t stride, int stage_rows) {
-    constexpr int RP = 16, NW = 16;
-    extern __shared__ float stage[];                   // [stage_rows][RP + 1]
-    __shared__ float Gs_all[NW][RP * (RP + 1)];
-    __shared__ float bs_all[NW][RP];
-    const int s = blockIdx.y, P = gridDim.x, p = blockIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
-    const int ns = smp.ncol[s];
-    const int nlines = rows_side ? ms : ns;
-    const int l0 = (int)((int64_t)nlines * p / P), l1 = (int)((int64_t)nlines * (p + 1) / P);
-    if (l0 >= l1) return;
-    const float* src = rows_side ? Fin + (int64_t)s * F.C * r : Fin + (int64_t)row0 * r;
-    const int nsrc = rows_side ? ns : ms;
-    const bool staged = nsrc <= stage_rows;
-    if (staged) {
-        if (r == RP) {  // 16-byte loads of whole factor rows
-            const float4* src4 = reinterpret_cast<const float4*>(src);
-            for (int i = threadIdx.x; i < nsrc * (RP / 4); i += blockDim.x) {
-                const int row = i / (RP / 4), c4 = i % (RP / 4);
-                const float4 v = __ldg(src4 + i);
-                float* d = stage + row * (RP + 1) + 4 * c4;
-                d[0] = v.x;
-                d[1] = v.y;
-                d[2] = v.z;
-                d[3] = v.w;
-            }
-        } else {
-            for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
-                const int row = i / RP, c = i % RP;
-                stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * r + c) : 0.f;
-            }
-        }
-    }
-    __syncthreads();
-    const float* Fb = staged ? stage : src;
-    const int fstride = staged ? RP + 1 : r;
-    const int64_t o = smp.off[s];
-    const int64_t gbase = rows_side ? (int64_t)row0 : om.line_pfx[s];
-    float* Gs = &Gs_all[wid][0];
-    float* bs = &bs_all[wid][0];
-    for (int line = l0 + wid; line < l1; line += NW) {
-        int len;
-        const uint16_t* idx;
-        const float* vv;
-        if (rows_side) {
-            const int32_t* rp = om.rp + row0 + s;
-            const int b = rp[line];
-            len = rp[line + 1] - b;
-            idx = om.cidx + o + b;
-            vv = om.cval + o + b;
-        } else {
-            const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
-            const int b = cp[line];
-            len = cp[line + 1] - b;
-            idx = om.ridx + o + b;
-            vv = om.rval + o + b;
-        }
-        gram_tc<RP>(len, idx, vv, Fb, fstride, r, Gs, bs);
-        __syncwarp();
-        const int64_t gl = gbase + line;
-        for (int q = lane; q < RP * RP; q += 32) {
-            const int i = q / RP, j = q % RP;
-            if (j <= i) Gg[(int64_t)(i * (i + 1) / 2 + j) * stride + gl] = Gs[i * (RP + 1) + j];
-        }
-        if (lane < RP) Gg[(int64_t)(136 + lane) * stride + gl] = bs[lane];
-        __syncwarp();
-    }
-}
-
-// Solve (G + lambda I) u = b for one line per thread.  T = float with a pivot check,
-// or T = double for the retry of the lines that fail it.
-template <typename T>
-__device__ __forceinline__ bool solve16(const float* __restrict__ Gg, int64_t stride, int64_t gl, int r,
-                                        float lam_rel, bool check, T* u) {
-    T a[136], b[16];
-#pragma unroll
-    for (int e = 0; e < 136; ++e) a[e] = (T)__ldg(Gg + (int64_t)e * stride + gl);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) b[i] = (T)__ldg(Gg + (int64_t)(136 + i) * stride + gl);
+// Cholesky solve of (G + lam I) u = b in place (u returned in b); rows i >= r are
+// identity rows with b_i = 0.  Returns false when `check` and the float pivots are
+// not acceptable (a non-positive pivot or min/max pivot^2 < kPivotRatio).
+template <int RP, typename T>
+__device__ __forceinline__ bool chol_solve(T (&a)[RP * (RP + 1) / 2], T (&b)[RP], int r, float lam_rel, bool check) {
     T tr = T(0);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) tr += a[i * (i + 1) / 2 + i];
-    if (!(tr > T(0))) {
+    for (int i = 0; i < RP; ++i) tr += a[i * (i + 1) / 2 + i];
+    if (!(tr > T(0))) {  // no observed entry (or all-zero factors): zero factor
 #pragma unroll
-        for (int i = 0; i < 16; ++i) u[i] = T(0);
+        for (int i = 0; i < RP; ++i) b[i] = T(0);
         return true;
     }
     const T lam = (T)lam_rel * tr / (T)r;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < RP; ++i) {
         if (i < r) {
             a[i * (i + 1) / 2 + i] += lam;
-        } else {  // padding: identity rows, zero right-hand side
+        } else {
 #pragma unroll
             for (int j = 0; j <= i; ++j) a[i * (i + 1) / 2 + j] = (j == i) ? T(1) : T(0);
             b[i] = T(0);
         }
     }
-    // Cholesky (Crout order), L overwrites the lower triangle
     T dmin = T(3.0e38), dmax = T(0);
     bool ok = true;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < RP; ++j) {
         T d = a[j * (j + 1) / 2 + j];
 #pragma unroll
         for (int k = 0; k < j; ++k) d -= a[j * (j + 1) / 2 + k] * a[j * (j + 1) / 2 + k];
@@ -590,7 +660,7 @@ __device__ __forceinline__ bool solve16(const float* __restrict__ Gg, int64_t st
         const T inv = T(1) / ljj;
         a[j * (j + 1) / 2 + j] = ljj;
 #pragma unroll
-        for (int i = j + 1; i < 16; ++i) {
+        for (int i = j + 1; i < RP; ++i) {
             T t = a[i * (i + 1) / 2 + j];
 #pragma unroll
             for (int k = 0; k < j; ++k) t -= a[i * (i + 1) / 2 + k] * a[j * (j + 1) / 2 + k];
@@ -599,64 +669,209 @@ __device__ __forceinline__ bool solve16(const float* __restrict__ Gg, int64_t st
     }
     if (check && (!ok || dmin < (T)kPivotRatio * dmax)) return false;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {  // L y = b
+    for (int i = 0; i < RP; ++i) {  // L y = b
         T t = b[i];
 #pragma unroll
         for (int k = 0; k < i; ++k) t -= a[i * (i + 1) / 2 + k] * b[k];
         b[i] = t / a[i * (i + 1) / 2 + i];
     }
 #pragma unroll
-    for (int i = 15; i >= 0; --i) {  // L^T x = y
+    for (int i = RP - 1; i >= 0; --i) {  // L^T x = y
         T t = b[i];
 #pragma unroll
-        for (int k = i + 1; k < 16; ++k) t -= a[k * (k + 1) / 2 + i] * b[k];
+        for (int k = i + 1; k < RP; ++k) t -= a[k * (k + 1) / 2 + i] * b[k];
         b[i] = t / a[i * (i + 1) / 2 + i];
     }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) u[i] = i < r ? b[i] : T(0);
     return true;
 }
 
-__device__ __forceinline__ int64_t solve_line_out(const lt_frame& F, const Omega& om, bool rows_side, int64_t t) {
-    if (rows_side) return t;
-    int lo = 0, hi = F.S;  // slice of compact column t
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (om.line_pfx[mid] <= t) lo = mid;
-        else hi = mid;
-    }
-    return (int64_t)lo * F.C + (t - om.line_pfx[lo]);
+// A staged factor row is RP floats (RP/4 16-byte slots).  Slot q of row j is stored
+// at slot q ^ h(j) so that the rows read by one quarter-warp (random j) spread over
+// all eight 16-byte bank groups of a 128-byte shared-memory wavefront.
+template <int RP>
+__device__ __forceinline__ int stage_slot(int j, int q) {
+    constexpr int NQ = RP / 4, RPB = 8 / NQ;  // slots per row, rows per wavefront
+    return j * NQ + (q ^ ((j / RPB) % NQ));
 }
 
-__global__ void __launch_bounds__(128) k_solve16(lt_frame F, Omega om, const float* __restrict__ Gg, int64_t stride,
-                                                 int r, float lam_rel, bool rows_side, float* __restrict__ Fout,
-                                                 uint8_t* __restrict__ retry) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nl = rows_side ? F.m : om.line_pfx[F.S];
-    if (t >= nl) return;
-    float u[16];
-    const bool ok = solve16<float>(Gg, stride, t, r, lam_rel, true, u);
-    retry[t] = ok ? 0 : 1;
-    if (!ok) return;
-    float* dst = Fout + solve_line_out(F, om, rows_side, t) * r;
+// Lower triangle of G = sum_e x_e x_e^T and b = sum_e a_e x_e of one line, in the
+// entries' stored order.
+// A lane of a group of G takes the entries e0, e0 + G, ... (e0 = its rank in the group).
+template <int RP>
+__device__ __forceinline__ void line_gram(int len, const uint16_t* __restrict__ idx, const float* __restrict__ vv,
+                                          int r, const float* __restrict__ src, bool staged, const float4* stage4,
+                                          float (&a)[RP * (RP + 1) / 2], float (&bb)[RP], int e0 = 0, int G = 1) {
+    constexpr int NA = RP * (RP + 1) / 2, NQ = RP / 4;
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-        if (i < r) dst[i] = u[i];
+    for (int i = 0; i < NA; ++i) a[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) bb[i] = 0.f;
+    // the loads of the next two entries are in flight during this one's FMAs
+    int jn = e0 < len ? (int)idx[e0] : 0, jn2 = e0 + G < len ? (int)idx[e0 + G] : 0;
+    float an = e0 < len ? vv[e0] : 0.f, an2 = e0 + G < len ? vv[e0 + G] : 0.f;
+    for (int e = e0; e < len; e += G) {
+        const int j = jn;
+        const float av = an;
+        jn = jn2;
+        an = an2;
+        if (e + 2 * G < len) {
+            jn2 = (int)idx[e + 2 * G];
+            an2 = vv[e + 2 * G];
+        }
+        float x[RP];
+        if (staged) {
+#pragma unroll
+            for (int c4 = 0; c4 < NQ; ++c4) {
+                const float4 t = stage4[stage_slot<RP>(j, c4)];
+                x[4 * c4] = t.x;
+                x[4 * c4 + 1] = t.y;
+                x[4 * c4 + 2] = t.z;
+                x[4 * c4 + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < RP; ++c) x[c] = c < r ? __ldg(src + (int64_t)j * r + c) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < RP; ++i) {
+            bb[i] = fmaf(av, x[i], bb[i]);
+#pragma unroll
+            for (int k = 0; k <= i; ++k) a[i * (i + 1) / 2 + k] = fmaf(x[i], x[k], a[i * (i + 1) / 2 + k]);
+        }
+    }
 }
 
-// float64 retry of the lines whose float pivots were not acceptable
-__global__ void __launch_bounds__(64) k_solve16_retry(lt_frame F, Omega om, const float* __restrict__ Gg,
-                                                      int64_t stride, int r, float lam_rel, bool rows_side,
-                                                      float* __restrict__ Fout, const uint8_t* __restrict__ retry,
-                                                      int32_t* n_fp64) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nl = rows_side ? F.m : om.line_pfx[F.S];
-    if (t >= nl || !retry[t]) return;
-    double u[16];
-    solve16<double>(Gg, stride, t, r, lam_rel, false, u);
-    float* dst = Fout + solve_line_out(F, om, rows_side, t) * r;
-    for (int i = 0; i < r && i < 16; ++i) dst[i] = (float)u[i];
-    atomicAdd(n_fp64, 1);
+template <int RP>
+__device__ __forceinline__ void als_line(const lt_frame& F, const lt_samples& smp, const Omega& om, int r,
+                                         bool rows_side, const float* __restrict__ src, bool staged,
+                                         const float4* stage4, float* __restrict__ Fout, float lam_rel,
+                                         const AlsQueue<RP>& q, int s, int line, int sub, int G);
+
+template <int RP>
+__global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp, Omega om, int r, bool rows_side,
+                                                    const float* __restrict__ Fin, float* __restrict__ Fout,
+                                                    float lam_rel, AlsQueue<RP> q, int stage_rows) {
+    constexpr int NQ = RP / 4;
+    extern __shared__ float4 stage4[];
+    const int s = blockIdx.y;
+    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
+    const int ns = smp.ncol[s];
+    const int nlines = rows_side ? ms : ns;
+    if ((int)(blockIdx.x * blockDim.x) >= nlines) return;
+    const float* src = rows_side ? Fin + (int64_t)s * F.C * r : Fin + (int64_t)row0 * r;
+    const int nsrc = rows_side ? ns : ms;
+    const bool staged = nsrc <= stage_rows;
+    if (staged) {
+        if (r == RP) {
+            const float4* src4 = reinterpret_cast<const float4*>(src);
+            for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x)
+                stage4[stage_slot<RP>(i / NQ, i % NQ)] = __ldg(src4 + i);
+        } else {
+            for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x) {
+                const int row = i / NQ, q4 = i % NQ;
+                float v[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[c] = 4 * q4 + c < r ? __ldg(src + (int64_t)row * r + 4 * q4 + c) : 0.f;
+                stage4[stage_slot<RP>(row, q4)] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        }
+    }
+    __syncthreads();
+    // warp tasks, heaviest class first, dealt round-robin over the slice's warps
+    const int32_t* ord = rows_side ? om.rord + row0 : om.cord + (int64_t)s * F.C;
+    const int32_t* cls = (rows_side ? om.rcls : om.ccls) + (int64_t)s * 16;
+    const int ntask = cls[8 + kClasses];
+    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int t = blockIdx.x * nwarp + (threadIdx.x >> 5); t < ntask; t += gridDim.x * nwarp) {
+        int k = 0;
+        while (k + 1 < kClasses && t >= cls[8 + k + 1]) ++k;
+        const int g = kClasses - 1 - k, G = 1 << g;
+        const int li = cls[k] + (t - cls[8 + k]) * (32 >> g) + (lane >> g);
+        const bool live = li < cls[k + 1];
+        als_line<RP>(F, smp, om, r, rows_side, src, staged, stage4, Fout, lam_rel, q, s, live ? ord[li] : -1,
+                     lane & (G - 1), G);
+    }
+}
+
+template <int RP>
+__device__ __forceinline__ void als_line(const lt_frame& F, const lt_samples& smp, const Omega& om, int r,
+                                         bool rows_side, const float* __restrict__ src, bool staged,
+                                         const float4* stage4, float* __restrict__ Fout, float lam_rel,
+                                         const AlsQueue<RP>& q, int s, int line, int sub, int G) {
+    constexpr int NA = RP * (RP + 1) / 2;
+    const int row0 = F.slice_off[s];
+    const int64_t o = smp.off[s];
+    int b0 = 0, len = 0;
+    const uint16_t* idx = nullptr;
+    const float* vv = nullptr;
+    if (line >= 0) {
+        if (rows_side) {
+            const int32_t* rp = om.rp + row0 + s;
+            b0 = rp[line];
+            len = rp[line + 1] - b0;
+            idx = om.cidx + o + b0;
+            vv = om.cval + o + b0;
+        } else {
+            const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
+            b0 = cp[line];
+            len = cp[line + 1] - b0;
+            idx = om.ridx + o + b0;
+            vv = om.rval + o + b0;
+        }
+    }
+    float a[NA], bb[RP];
+    line_gram<RP>(len, idx, vv, r, src, staged, stage4, a, bb, sub, G);
+    if (G > 1) {  // the group's partial sums into its first lane (G is warp-uniform)
+        for (int m = G >> 1; m > 0; m >>= 1) {
+#pragma unroll
+            for (int i = 0; i < NA; ++i) a[i] += __shfl_down_sync(0xffffffffu, a[i], m, G);
+#pragma unroll
+            for (int i = 0; i < RP; ++i) bb[i] += __shfl_down_sync(0xffffffffu, bb[i], m, G);
+        }
+    }
+    if (line < 0 || sub != 0) return;
+    const int64_t dst = rows_side ? (int64_t)(row0 + line) * r : ((int64_t)s * F.C + line) * r;
+    if (chol_solve<RP, float>(a, bb, r, lam_rel, true)) {
+#pragma unroll
+        for (int i = 0; i < RP; ++i)
+            if (i < r) Fout[dst + i] = bb[i];
+        return;
+    }
+    // rare: queue the Gram (accumulated again, in the same order) for float64
+    const int slot = atomicAdd(q.count, 1);
+    if (slot >= q.cap) {
+        latch(q.status, LT_ELIMIT);
+        return;
+    }
+    line_gram<RP>(len, idx, vv, r, src, staged, stage4, a, bb);  // whole line, this lane alone
+    q.dst[slot] = dst;
+    float* gq = q.gram + (int64_t)slot * AlsQueue<RP>::kVals;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) gq[i] = a[i];
+#pragma unroll
+    for (int i = 0; i < RP; ++i) gq[NA + i] = bb[i];
+}
+
+// float64 solve of the queued lines (grid-stride over the device count)
+template <int RP>
+__global__ void __launch_bounds__(64) k_als_retry(AlsQueue<RP> q, int r, float lam_rel, float* __restrict__ Fout,
+                                                  int32_t* __restrict__ n_fp64) {
+    constexpr int NA = RP * (RP + 1) / 2;
+    const int n = min((int64_t)*q.count, q.cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const float* gq = q.gram + (int64_t)t * AlsQueue<RP>::kVals;
+        double a[NA], b[RP];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) a[i] = gq[i];
+#pragma unroll
+        for (int i = 0; i < RP; ++i) b[i] = gq[NA + i];
+        chol_solve<RP, double>(a, b, r, lam_rel, false);
+        float* d = Fout + q.dst[t];
+#pragma unroll
+        for (int i = 0; i < RP; ++i)
+            if (i < r) d[i] = (float)b[i];
+        atomicAdd(n_fp64, 1);
+    }
 }
 
 __global__ void k_render(lt_frame F, lt_samples smp, const float* __restrict__ U, const float* __restrict__ V,
@@ -719,7 +934,8 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     lt_status st;
     char* p = (char*)lt_scratch(ctx, SCR_OMEGA,
                                 (size_t)(f->m + S) * 4 + (size_t)S * (C + 1) * 4 + (size_t)E * 12 + S * 8 +
-                                    (size_t)S * (om.bm_stride + om.bt_stride) * 8 + (S + 1) * 8 + 16 * 256,
+                                    (size_t)S * (om.bm_stride + om.bt_stride) * 8 + (S + 1) * 8 + (size_t)f->m * 4 +
+                                    (size_t)S * C * 4 + (size_t)S * 128 + 16 * 256,
                                 &st);
     if (!p) return st;
     auto take = [&](size_t nbytes) {
@@ -739,55 +955,86 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.wr = (uint32_t*)take((size_t)S * om.bm_stride * 4);
     om.wc = (uint32_t*)take((size_t)S * om.bt_stride * 4);
     om.line_pfx = (int64_t*)take((S + 1) * 8);
-    int32_t* n64 = (int32_t*)lt_scratch(ctx, SCR_ALS, 256, &st);
-    if (!n64) return st;
-    LT_CUDA(ctx, cudaMemsetAsync(n64, 0, 4, ctx->stream));
-    k_omega<<<S, 1024, 0, ctx->stream>>>(*f, *smp, om, ctx->d_status);
-    LT_LAUNCH_CHECK(ctx, "k_omega");
+    om.rord = (int32_t*)take((size_t)f->m * 4);
+    om.cord = (int32_t*)take((size_t)S * C * 4);
+    om.rcls = (int32_t*)take((size_t)S * 16 * 4);
+    om.ccls = (int32_t*)take((size_t)S * 16 * 4);
+    const int r = uv->r;
+    const int RP = r <= 8 ? 8 : r <= 16 ? 16 : 32;
+    // per half-step retry counters, the float64 count, the mean partials
+    constexpr int kOmParts = 8;
+    const int nq = std::max(1, 2 * iters);
+    char* sp = (char*)lt_scratch(ctx, SCR_ALS, (size_t)(nq + 64) * 4 + (size_t)S * kOmParts * 4 + 512, &st);
+    if (!sp) return st;
+    int32_t* n64 = (int32_t*)sp;
+    int32_t* qcount = n64 + 64;
+    float* part = (float*)(sp + (((size_t)(nq + 64) * 4 + 255) & ~(size_t)255));
+    LT_CUDA(ctx, cudaMemsetAsync(n64, 0, (size_t)(nq + 64) * 4, ctx->stream));
+    const int nsm = ctx->num_sms;
+    k_om_clear<<<dim3(std::max(1, 2 * nsm / S), S), 256, 0, ctx->stream>>>(*f, *smp, om);
+    LT_LAUNCH_CHECK(ctx, "k_om_clear");
+    k_om_bits<<<dim3(kOmParts, S), 256, 0, ctx->stream>>>(*f, *smp, om, part, ctx->d_status);
+    LT_LAUNCH_CHECK(ctx, "k_om_bits");
+    k_om_lines<<<dim3(std::max(1, 4 * nsm / S), S), 256, 0, ctx->stream>>>(*f, *smp, om);
+    LT_LAUNCH_CHECK(ctx, "k_om_lines");
+    k_om_scan<<<S, 1024, 0, ctx->stream>>>(*f, *smp, om, part, kOmParts);
+    LT_LAUNCH_CHECK(ctx, "k_om_scan");
+    k_om_scatter<<<dim3(std::max(1, 4 * nsm / S), S), 256, 0, ctx->stream>>>(*f, *smp, om);
+    LT_LAUNCH_CHECK(ctx, "k_om_scatter");
     k_line_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, S, om.line_pfx);
     LT_LAUNCH_CHECK(ctx, "k_line_prefix");
-    const int r = uv->r;
     k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, r, seed_ref(ctx, seed), uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
-    // CTAs per slice: about two per SM over the whole grid
-    const int P = std::max(1, (2 * ctx->num_sms + S - 1) / S);
-    const int RP = r <= 16 ? 16 : 32;
-    // static shared memory of the kernel per CTA, the rest of 200 KB stages factor rows
-    const size_t stat = (size_t)(RP == 32 ? 8 : 16) * (32 / RP) * (RP * (RP + 1) + RP) * 4;
-    const size_t budget = (size_t)210 * 1024 > stat ? (size_t)210 * 1024 - stat : 0;
-    const int stage_rows = (int)std::min<size_t>(budget / ((RP + 1) * 4), (size_t)1 << 20);
-    const size_t dyn = (size_t)stage_rows * (RP + 1) * 4;
-    if (RP == 32)
-        LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    if (RP == 16) {
-        // Gram buffer: element-major, one column per line (rows or compact columns)
-        const int64_t stride = std::max<int64_t>(f->m, (int64_t)S * C);
-        char* gp = (char*)lt_scratch(ctx, SCR_GRAM, (size_t)kGramVals * stride * 4 + stride + 256, &st);
-        if (!gp) return st;
-        float* Gg = (float*)gp;
-        uint8_t* retry = (uint8_t*)(gp + (size_t)kGramVals * stride * 4);
-        const size_t gstat = (size_t)16 * (17 * 16 + 16) * 4;
-        const int grows = (int)(((size_t)210 * 1024 - gstat) / (17 * 4));
-        const size_t gdyn = (size_t)grows * 17 * 4;
-        LT_CUDA(ctx, cudaFuncSetAttribute(k_gram16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gdyn));
+    if (RP <= 16) {
+        // one thread per line; one 256-thread CTA per SM stages the slice's factor
+        // rows (up to 110 KB) in shared memory and leaves the rest of the SM's
+        // 256 KB to L1 for the lines' entry streams
+        const size_t row_bytes = (size_t)RP * 4;
+        const int stage_rows = (int)std::min<int64_t>((110 * 1024) / row_bytes, std::max<int64_t>(mr, C));
+        const size_t dyn = (size_t)stage_rows * row_bytes;
+        const int64_t cap = std::min<int64_t>(std::max<int64_t>(f->m, (int64_t)S * C), 1 << 18);
+        const int kv = RP * (RP + 1) / 2 + RP;
+        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, (size_t)cap * (8 + (size_t)kv * 4) + 512, &st);
+        if (!qp) return st;
+        int64_t* qdst = (int64_t*)qp;
+        float* qgram = (float*)(qp + (((size_t)cap * 8 + 255) & ~(size_t)255));
+        const unsigned gx = (unsigned)std::max<int64_t>(1, (mr + 255) / 256);
         for (int it = 0; it < iters; ++it) {
             for (int side = 0; side < 2; ++side) {
                 const bool rows = side == 0;
                 const float* fin = rows ? uv->V : uv->U;
                 float* fout = rows ? uv->U : uv->V;
-                k_gram16<<<dim3(P, S), 512, gdyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, Gg, stride, grows);
-                LT_LAUNCH_CHECK(ctx, "k_gram16");
-                const int64_t nl = rows ? f->m : (int64_t)S * C;
-                k_solve16<<<(unsigned)((nl + 127) / 128), 128, 0, ctx->stream>>>(*f, om, Gg, stride, r, lam_rel, rows,
-                                                                                  fout, retry);
-                LT_LAUNCH_CHECK(ctx, "k_solve16");
-                k_solve16_retry<<<(unsigned)((nl + 63) / 64), 64, 0, ctx->stream>>>(*f, om, Gg, stride, r, lam_rel,
-                                                                                    rows, fout, retry, n64);
-                LT_LAUNCH_CHECK(ctx, "k_solve16_retry");
+                int32_t* cnt = qcount + 2 * it + side;
+                if (RP == 8) {
+                    AlsQueue<8> q{cnt, qdst, qgram, cap, ctx->d_status};
+                    LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)dyn));
+                    k_als_line<8><<<dim3(gx, S), 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout, lam_rel,
+                                                                          q, stage_rows);
+                    LT_LAUNCH_CHECK(ctx, "k_als_line");
+                    k_als_retry<8><<<2 * nsm, 64, 0, ctx->stream>>>(q, r, lam_rel, fout, n64);
+                    LT_LAUNCH_CHECK(ctx, "k_als_retry");
+                } else {
+                    AlsQueue<16> q{cnt, qdst, qgram, cap, ctx->d_status};
+                    LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)dyn));
+                    k_als_line<16><<<dim3(gx, S), 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout,
+                                                                           lam_rel, q, stage_rows);
+                    LT_LAUNCH_CHECK(ctx, "k_als_line");
+                    k_als_retry<16><<<2 * nsm, 64, 0, ctx->stream>>>(q, r, lam_rel, fout, n64);
+                    LT_LAUNCH_CHECK(ctx, "k_als_retry");
+                }
             }
         }
         return LT_OK;
     }
+    // r > 16: one warp group per line on the tensor cores
+    const int P = std::max(1, (2 * ctx->num_sms + S - 1) / S);
+    const size_t stat = (size_t)8 * (RP * (RP + 1) + RP) * 4;
+    const size_t budget = (size_t)210 * 1024 > stat ? (size_t)210 * 1024 - stat : 0;
+    const int stage_rows = (int)std::min<size_t>(budget / ((RP + 1) * 4), (size_t)1 << 20);
+    const size_t dyn = (size_t)stage_rows * (RP + 1) * 4;
+    LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     for (int it = 0; it < iters; ++it) {
         for (int side = 0; side < 2; ++side) {
             const bool rows = side == 0;
