@@ -41,6 +41,24 @@ struct Omega {
     int32_t* cord;      // [S][C]       columns of each slice by decreasing entry count
     int32_t* rcls;      // [S][16]      per group-size class g: first sorted row, first warp task
     int32_t* ccls;      // [S][16]      the same for the columns
+    // Sliced layout of the lane-group ALS (r <= 16), one per side: the entry streams
+    // of the 32 lanes of a warp task interleaved in chunks of 4, entry kk of lane l at
+    // base[s] + tb[t] + 128 (kk / 4) + 4 l + kk % 4, so that a lane reads 4 entries
+    // with one 8-byte and one 16-byte load and a warp's loads are coalesced.
+    int32_t* rpos;      // [m]          sorted position of each row
+    int32_t* cpos;      // [S][C]       sorted position of each column
+    int32_t* rtb;       // [S][tcap]    offset of each rows-side warp task in its slice's region
+    int32_t* ctb;       // [S][tcap]
+    int64_t* rbase;     // [S + 1]      region start of each slice, rows side ([S] = total)
+    int64_t* cbase;     // [S + 1]
+    uint16_t* sidx_r;   // [sell_cap]   column of each rows-side slot
+    float* sval_r;
+    uint16_t* sidx_c;   // [sell_cap]   row of each columns-side slot
+    float* sval_c;
+    int64_t sell_cap;
+    int tcap;
+    bool sell;          // fill the sliced layout
+    bool csr;           // fill CSR / CSC (the warp-group ALS for r > 16)
 };
 
 // Group-size classes of a line: class g gives a line of L entries G = 2^g lanes, so
@@ -217,16 +235,66 @@ __device__ void om_order(const int32_t* __restrict__ cnt1, int n, int32_t* __res
     __syncthreads();
 }
 
+// run of the sorted order that holds position li (classes largest first)
+__device__ __forceinline__ int om_run(const int32_t* cls, int li) {
+    int k = 0;
+    while (k + 1 < kClasses && li >= cls[k + 1]) ++k;
+    return k;
+}
+
+// pos[ord[i]] = i, and the sliced layout of one side: a class-g task covers
+// P = 32 / 2^g lines, its lanes hold ceil(count / 2^g) slots at most, so the task
+// takes 32 x (that maximum over its lines, rounded up to 4) slots; tb[t] = the
+// slots before task t (a multiple of 128).
+// The region size goes to *size.
+__device__ void om_tasks(const int32_t* __restrict__ cnt1, int n, const int32_t* __restrict__ ord,
+                         const int32_t* __restrict__ cls, int32_t* __restrict__ pos, int32_t* __restrict__ tb,
+                         int64_t* size, int32_t* ws) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) pos[ord[i]] = i;
+    const int T = cls[8 + kClasses];
+    int carry = 0;
+    for (int t0 = 0; t0 < T; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        int w = 0;
+        if (t < T) {
+            int k = 0;
+            while (k + 1 < kClasses && t >= cls[8 + k + 1]) ++k;
+            const int g = kClasses - 1 - k, G = 1 << g, P = 32 >> g;
+            const int li0 = cls[k] + (t - cls[8 + k]) * P, li1 = min(li0 + P, cls[k + 1]);
+            int kk = 0;
+            for (int li = li0; li < li1; ++li) kk = max(kk, (cnt1[ord[li]] + G - 1) >> g);
+            w = 32 * ((kk + 3) & ~3);
+        }
+        int tot;
+        const int pre = block_exclusive_scan<int>(w, ws, &tot);
+        if (t < T) tb[t] = carry + pre;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *size = carry;
+    __syncthreads();
+}
+
 __global__ void k_om_scan(lt_frame F, lt_samples smp, Omega om, const float* __restrict__ part, int nparts) {
     __shared__ int32_t ws[32];
     __shared__ unsigned long long key[kOrdMax];
     const int s = blockIdx.x;
     const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0, ns = smp.ncol[s], ne = smp.cnt[s];
-    om_order(om.rp + row0 + s + 1, ms, om.rord + row0, key);
-    om_classes(om.rp + row0 + s + 1, ms, om.rord + row0, ms <= kOrdMax, om.rcls + (int64_t)s * 16);
-    om_order(om.cp + (int64_t)s * (F.C + 1) + 1, ns, om.cord + (int64_t)s * F.C, key);
-    om_classes(om.cp + (int64_t)s * (F.C + 1) + 1, ns, om.cord + (int64_t)s * F.C, ns <= kOrdMax,
-               om.ccls + (int64_t)s * 16);
+    const int32_t* rc1 = om.rp + row0 + s + 1;                // row counts (before the scan)
+    const int32_t* cc1 = om.cp + (int64_t)s * (F.C + 1) + 1;  // column counts
+    int32_t* rord = om.rord + row0;
+    int32_t* cord = om.cord + (int64_t)s * F.C;
+    int32_t* rcls = om.rcls + (int64_t)s * 16;
+    int32_t* ccls = om.ccls + (int64_t)s * 16;
+    om_order(rc1, ms, rord, key);
+    om_classes(rc1, ms, rord, ms <= kOrdMax, rcls);
+    om_order(cc1, ns, cord, key);
+    om_classes(cc1, ns, cord, ns <= kOrdMax, ccls);
+    if (om.sell) {
+        om_tasks(rc1, ms, rord, rcls, om.rpos + row0, om.rtb + (int64_t)s * om.tcap, om.rbase + s + 1, ws);
+        om_tasks(cc1, ns, cord, ccls, om.cpos + (int64_t)s * F.C, om.ctb + (int64_t)s * om.tcap, om.cbase + s + 1,
+                 ws);
+    }
     om_scan_counts(om.rp + row0 + s, ms, ws);
     om_scan_counts(om.cp + (int64_t)s * (F.C + 1), ns, ws);
     if (threadIdx.x == 0) {
@@ -234,6 +302,41 @@ __global__ void k_om_scan(lt_frame F, lt_samples smp, Omega om, const float* __r
         for (int q = 0; q < nparts; ++q) t += part[(int64_t)s * nparts + q];
         om.mu[s] = ne > 0 ? t / (float)ne : 0.f;
     }
+}
+
+// region starts of the sliced layouts: in place, x[1..S] sizes -> x[0..S] prefix;
+// a total beyond the capacity latches LT_ELIMIT (the scatter then skips slots past it)
+__global__ void k_om_sellpfx(int S, Omega om, int32_t* status) {
+    __shared__ int64_t ws[32];
+    for (int side = 0; side < 2; ++side) {
+        int64_t* x = side == 0 ? om.rbase : om.cbase;
+        int64_t carry = 0;
+        for (int i0 = 0; i0 < S; i0 += blockDim.x) {
+            const int i = i0 + threadIdx.x;
+            const int64_t c = i < S ? x[i + 1] : 0;
+            int64_t tot;
+            const int64_t pre = block_exclusive_scan<int64_t>(c, ws, &tot);
+            if (i < S) x[i + 1] = carry + pre + c;
+            carry += tot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            x[0] = 0;
+            if (carry > om.sell_cap) latch(status, LT_ELIMIT);
+        }
+        __syncthreads();
+    }
+}
+
+// slot, within the slice's region, of entry k of the line at sorted position li
+__device__ __forceinline__ int64_t sell_slot(const int32_t* __restrict__ cls, const int32_t* __restrict__ tb, int li,
+                                             int k) {
+    const int run = om_run(cls, li);
+    const int g = kClasses - 1 - run, P = 32 >> g;
+    const int rel = li - cls[run];
+    const int t = cls[8 + run] + rel / P, lane = (rel % P) * (1 << g) + (k & ((1 << g) - 1));
+    const int kk = k >> g;
+    return (int64_t)tb[t] + 128 * (int64_t)(kk >> 2) + 4 * lane + (kk & 3);
 }
 
 __global__ void k_om_scatter(lt_frame F, lt_samples smp, Omega om) {
@@ -254,13 +357,29 @@ __global__ void k_om_scatter(lt_frame F, lt_samples smp, Omega om) {
         const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
         if (r >= ms || c >= ns) continue;
         const int64_t iw = (int64_t)r * W + (c >> 5), jw = (int64_t)c * WT + (r >> 5);
-        const int pr = rp[r] + (int)wr[iw] + __popc(bm[iw] & ((1u << (c & 31)) - 1u));
-        const int pc = cp[c] + (int)wc[jw] + __popc(bt[jw] & ((1u << (r & 31)) - 1u));
+        const int kr = (int)wr[iw] + __popc(bm[iw] & ((1u << (c & 31)) - 1u));  // index in its row
+        const int kc = (int)wc[jw] + __popc(bt[jw] & ((1u << (r & 31)) - 1u));  // index in its column
         const float v = val[e];
-        om.cidx[o + pr] = (uint16_t)c;
-        om.cval[o + pr] = v;
-        om.ridx[o + pc] = (uint16_t)r;
-        om.rval[o + pc] = v;
+        if (om.csr) {
+            om.cidx[o + rp[r] + kr] = (uint16_t)c;
+            om.cval[o + rp[r] + kr] = v;
+            om.ridx[o + cp[c] + kc] = (uint16_t)r;
+            om.rval[o + cp[c] + kc] = v;
+        }
+        if (om.sell) {
+            const int64_t pr = sell_slot(om.rcls + (int64_t)s * 16, om.rtb + (int64_t)s * om.tcap,
+                                         om.rpos[row0 + r], kr) + om.rbase[s];
+            const int64_t pc = sell_slot(om.ccls + (int64_t)s * 16, om.ctb + (int64_t)s * om.tcap,
+                                         om.cpos[(int64_t)s * F.C + c], kc) + om.cbase[s];
+            if (pr < om.sell_cap) {
+                om.sidx_r[pr] = (uint16_t)c;
+                om.sval_r[pr] = v;
+            }
+            if (pc < om.sell_cap) {
+                om.sidx_c[pc] = (uint16_t)r;
+                om.sval_c[pc] = v;
+            }
+        }
     }
 }
 
@@ -694,133 +813,89 @@ __device__ __forceinline__ int stage_slot(int j, int q) {
     return j * NQ + (q ^ ((j / RPB) % NQ));
 }
 
-// Lower triangle of G = sum_e x_e x_e^T and b = sum_e a_e x_e of one line, in the
-// entries' stored order.
-// A lane of a group of G takes the entries e0, e0 + G, ... (e0 = its rank in the group).
+// Adds x_e x_e^T (lower triangle) and a_e x_e for the nk entries of one lane's
+// stream (chunks of 4 at idx4[32 c], vv4[32 c]) to a and bb, in stream order.
 template <int RP>
-__device__ __forceinline__ void line_gram(int len, const uint16_t* __restrict__ idx, const float* __restrict__ vv,
-                                          int r, const float* __restrict__ src, bool staged, const float4* stage4,
-                                          float (&a)[RP * (RP + 1) / 2], float (&bb)[RP], int e0 = 0, int G = 1) {
-    constexpr int NA = RP * (RP + 1) / 2, NQ = RP / 4;
+__device__ __forceinline__ void stream_gram(int nk, const uint2* __restrict__ idx4, const float4* __restrict__ vv4,
+                                            int r, const float* __restrict__ src, bool staged, const float4* stage4,
+                                            float (&a)[RP * (RP + 1) / 2], float (&bb)[RP]) {
+    constexpr int NQ = RP / 4;
+    const int nc = (nk + 3) >> 2;
+    // the next two chunks' loads are in flight during this chunk's four entries
+    uint2 ic = nc > 0 ? idx4[0] : make_uint2(0u, 0u), in = nc > 1 ? idx4[32] : ic;
+    float4 vc = nc > 0 ? vv4[0] : make_float4(0.f, 0.f, 0.f, 0.f), vn = nc > 1 ? vv4[32] : vc;
+    for (int c = 0; c < nc; ++c) {
+        uint2 in2 = in;
+        float4 vn2 = vn;
+        if (c + 2 < nc) {
+            in2 = idx4[32 * (c + 2)];
+            vn2 = vv4[32 * (c + 2)];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (4 * c + q < nk) {
+                const uint32_t w = q < 2 ? ic.x : ic.y;
+                const int j = (int)((w >> (16 * (q & 1))) & 0xffffu);
+                const float av = q == 0 ? vc.x : q == 1 ? vc.y : q == 2 ? vc.z : vc.w;
+                float x[RP];
+                if (staged) {
+#pragma unroll
+                    for (int c4 = 0; c4 < NQ; ++c4) {
+                        const float4 t = stage4[stage_slot<RP>(j, c4)];
+                        x[4 * c4] = t.x;
+                        x[4 * c4 + 1] = t.y;
+                        x[4 * c4 + 2] = t.z;
+                        x[4 * c4 + 3] = t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int cc = 0; cc < RP; ++cc) x[cc] = cc < r ? __ldg(src + (int64_t)j * r + cc) : 0.f;
+                }
+#pragma unroll
+                for (int i = 0; i < RP; ++i) {
+                    bb[i] = fmaf(av, x[i], bb[i]);
+#pragma unroll
+                    for (int k = 0; k <= i; ++k)
+                        a[i * (i + 1) / 2 + k] = fmaf(x[i], x[k], a[i * (i + 1) / 2 + k]);
+                }
+            }
+        }
+        ic = in;
+        vc = vn;
+        in = in2;
+        vn = vn2;
+    }
+}
+
+// One lane of a warp task: `line` (or -1) is its line, `sub` its rank among the G
+// lanes of the line, `slot` the first slot of its stream (task base + 4 lane).
+template <int RP>
+__device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int r, bool rows_side,
+                                         const float* __restrict__ src, bool staged, const float4* stage4,
+                                         float* __restrict__ Fout, float lam_rel, const AlsQueue<RP>& q, int s,
+                                         int line, int sub, int G, int64_t slot) {
+    constexpr int NA = RP * (RP + 1) / 2;
+    const int row0 = F.slice_off[s];
+    int len = 0;
+    if (line >= 0) {
+        if (rows_side) {
+            const int32_t* rp = om.rp + row0 + s;
+            len = rp[line + 1] - rp[line];
+        } else {
+            const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
+            len = cp[line + 1] - cp[line];
+        }
+    }
+    const uint16_t* sidx = rows_side ? om.sidx_r : om.sidx_c;
+    const float* sval = rows_side ? om.sval_r : om.sval_c;
+    float a[NA], bb[RP];
 #pragma unroll
     for (int i = 0; i < NA; ++i) a[i] = 0.f;
 #pragma unroll
     for (int i = 0; i < RP; ++i) bb[i] = 0.f;
-    // the loads of the next two entries are in flight during this one's FMAs
-    int jn = e0 < len ? (int)idx[e0] : 0, jn2 = e0 + G < len ? (int)idx[e0 + G] : 0;
-    float an = e0 < len ? vv[e0] : 0.f, an2 = e0 + G < len ? vv[e0 + G] : 0.f;
-    for (int e = e0; e < len; e += G) {
-        const int j = jn;
-        const float av = an;
-        jn = jn2;
-        an = an2;
-        if (e + 2 * G < len) {
-            jn2 = (int)idx[e + 2 * G];
-            an2 = vv[e + 2 * G];
-        }
-        float x[RP];
-        if (staged) {
-#pragma unroll
-            for (int c4 = 0; c4 < NQ; ++c4) {
-                const float4 t = stage4[stage_slot<RP>(j, c4)];
-                x[4 * c4] = t.x;
-                x[4 * c4 + 1] = t.y;
-                x[4 * c4 + 2] = t.z;
-                x[4 * c4 + 3] = t.w;
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < RP; ++c) x[c] = c < r ? __ldg(src + (int64_t)j * r + c) : 0.f;
-        }
-#pragma unroll
-        for (int i = 0; i < RP; ++i) {
-            bb[i] = fmaf(av, x[i], bb[i]);
-#pragma unroll
-            for (int k = 0; k <= i; ++k) a[i * (i + 1) / 2 + k] = fmaf(x[i], x[k], a[i * (i + 1) / 2 + k]);
-        }
-    }
-}
-
-template <int RP>
-__device__ __forceinline__ void als_line(const lt_frame& F, const lt_samples& smp, const Omega& om, int r,
-                                         bool rows_side, const float* __restrict__ src, bool staged,
-                                         const float4* stage4, float* __restrict__ Fout, float lam_rel,
-                                         const AlsQueue<RP>& q, int s, int line, int sub, int G);
-
-template <int RP>
-__global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp, Omega om, int r, bool rows_side,
-                                                    const float* __restrict__ Fin, float* __restrict__ Fout,
-                                                    float lam_rel, AlsQueue<RP> q, int stage_rows) {
-    constexpr int NQ = RP / 4;
-    extern __shared__ float4 stage4[];
-    const int s = blockIdx.y;
-    const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
-    const int ns = smp.ncol[s];
-    const int nlines = rows_side ? ms : ns;
-    if ((int)(blockIdx.x * blockDim.x) >= nlines) return;
-    const float* src = rows_side ? Fin + (int64_t)s * F.C * r : Fin + (int64_t)row0 * r;
-    const int nsrc = rows_side ? ns : ms;
-    const bool staged = nsrc <= stage_rows;
-    if (staged) {
-        if (r == RP) {
-            const float4* src4 = reinterpret_cast<const float4*>(src);
-            for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x)
-                stage4[stage_slot<RP>(i / NQ, i % NQ)] = __ldg(src4 + i);
-        } else {
-            for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x) {
-                const int row = i / NQ, q4 = i % NQ;
-                float v[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) v[c] = 4 * q4 + c < r ? __ldg(src + (int64_t)row * r + 4 * q4 + c) : 0.f;
-                stage4[stage_slot<RP>(row, q4)] = make_float4(v[0], v[1], v[2], v[3]);
-            }
-        }
-    }
-    __syncthreads();
-    // warp tasks, heaviest class first, dealt round-robin over the slice's warps
-    const int32_t* ord = rows_side ? om.rord + row0 : om.cord + (int64_t)s * F.C;
-    const int32_t* cls = (rows_side ? om.rcls : om.ccls) + (int64_t)s * 16;
-    const int ntask = cls[8 + kClasses];
-    const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (int t = blockIdx.x * nwarp + (threadIdx.x >> 5); t < ntask; t += gridDim.x * nwarp) {
-        int k = 0;
-        while (k + 1 < kClasses && t >= cls[8 + k + 1]) ++k;
-        const int g = kClasses - 1 - k, G = 1 << g;
-        const int li = cls[k] + (t - cls[8 + k]) * (32 >> g) + (lane >> g);
-        const bool live = li < cls[k + 1];
-        als_line<RP>(F, smp, om, r, rows_side, src, staged, stage4, Fout, lam_rel, q, s, live ? ord[li] : -1,
-                     lane & (G - 1), G);
-    }
-}
-
-template <int RP>
-__device__ __forceinline__ void als_line(const lt_frame& F, const lt_samples& smp, const Omega& om, int r,
-                                         bool rows_side, const float* __restrict__ src, bool staged,
-                                         const float4* stage4, float* __restrict__ Fout, float lam_rel,
-                                         const AlsQueue<RP>& q, int s, int line, int sub, int G) {
-    constexpr int NA = RP * (RP + 1) / 2;
-    const int row0 = F.slice_off[s];
-    const int64_t o = smp.off[s];
-    int b0 = 0, len = 0;
-    const uint16_t* idx = nullptr;
-    const float* vv = nullptr;
-    if (line >= 0) {
-        if (rows_side) {
-            const int32_t* rp = om.rp + row0 + s;
-            b0 = rp[line];
-            len = rp[line + 1] - b0;
-            idx = om.cidx + o + b0;
-            vv = om.cval + o + b0;
-        } else {
-            const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
-            b0 = cp[line];
-            len = cp[line + 1] - b0;
-            idx = om.ridx + o + b0;
-            vv = om.rval + o + b0;
-        }
-    }
-    float a[NA], bb[RP];
-    line_gram<RP>(len, idx, vv, r, src, staged, stage4, a, bb, sub, G);
+    const int nk = sub < len ? (len - sub + G - 1) / G : 0;
+    stream_gram<RP>(nk, reinterpret_cast<const uint2*>(sidx + slot), reinterpret_cast<const float4*>(sval + slot), r,
+                    src, staged, stage4, a, bb);
     if (G > 1) {  // the group's partial sums into its first lane (G is warp-uniform)
         for (int m = G >> 1; m > 0; m >>= 1) {
 #pragma unroll
@@ -837,19 +912,152 @@ __device__ __forceinline__ void als_line(const lt_frame& F, const lt_samples& sm
             if (i < r) Fout[dst + i] = bb[i];
         return;
     }
-    // rare: queue the Gram (accumulated again, in the same order) for float64
-    const int slot = atomicAdd(q.count, 1);
-    if (slot >= q.cap) {
+    // rare: queue the Gram (accumulated again by this lane over the G streams) for float64
+    const int qs = atomicAdd(q.count, 1);
+    if (qs >= q.cap) {
         latch(q.status, LT_ELIMIT);
         return;
     }
-    line_gram<RP>(len, idx, vv, r, src, staged, stage4, a, bb);  // whole line, this lane alone
-    q.dst[slot] = dst;
-    float* gq = q.gram + (int64_t)slot * AlsQueue<RP>::kVals;
+#pragma unroll
+    for (int i = 0; i < NA; ++i) a[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < RP; ++i) bb[i] = 0.f;
+    for (int u = 0; u < G; ++u)
+        stream_gram<RP>(u < len ? (len - u + G - 1) / G : 0, reinterpret_cast<const uint2*>(sidx + slot + 4 * u),
+                        reinterpret_cast<const float4*>(sval + slot + 4 * u), r, src, staged, stage4, a, bb);
+    q.dst[qs] = dst;
+    float* gq = q.gram + (int64_t)qs * AlsQueue<RP>::kVals;
 #pragma unroll
     for (int i = 0; i < NA; ++i) gq[i] = a[i];
 #pragma unroll
     for (int i = 0; i < RP; ++i) gq[NA + i] = bb[i];
+}
+
+// stage the slice's source factor rows (nsrc x r, zero-padded to RP) in shared memory
+template <int RP>
+__device__ __forceinline__ void stage_factors(const float* __restrict__ src, int nsrc, int r, float4* stage4) {
+    constexpr int NQ = RP / 4;
+    if (r == RP) {
+        const float4* src4 = reinterpret_cast<const float4*>(src);
+        for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x)
+            stage4[stage_slot<RP>(i / NQ, i % NQ)] = __ldg(src4 + i);
+    } else {
+        for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x) {
+            const int row = i / NQ, q4 = i % NQ;
+            float v[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) v[c] = 4 * q4 + c < r ? __ldg(src + (int64_t)row * r + 4 * q4 + c) : 0.f;
+            stage4[stage_slot<RP>(row, q4)] = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+}
+
+// Persistent half-step: one CTA per SM.  CTA c owns the warp tasks (all slices, in
+// slice order) whose first slot lies in its equal share [lo, hi) of all the slots
+// of the side; for each slice it touches it stages the source factor rows once and
+// its warps take that slice's tasks from a shared counter.
+template <int RP>
+__global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp, Omega om, int r, bool rows_side,
+                                                    const float* __restrict__ Fin, float* __restrict__ Fout,
+                                                    float lam_rel, AlsQueue<RP> q, int stage_rows) {
+    extern __shared__ float4 stage4[];
+    __shared__ int s_next, s_t0, s_t1, s_slice;
+    const int S = F.S;
+    const int64_t* base = rows_side ? om.rbase : om.cbase;
+    const int64_t total = base[S];
+    // a layout over its capacity was latched as LT_ELIMIT and not written: read nothing
+    if (total > om.sell_cap) return;
+    const int64_t lo = total * blockIdx.x / gridDim.x;
+    const int64_t hi = blockIdx.x + 1 == gridDim.x ? INT64_MAX : total * (blockIdx.x + 1) / gridDim.x;
+    const int lane = threadIdx.x & 31;
+    int s = -1, t = 0;  // next task to consider (thread 0's view, shared through s_*)
+    if (threadIdx.x == 0) {
+        // Task starts are non-decreasing in (slice, task) order and every task of slice
+        // s starts at or before base[s + 1]: the first slice with base[s + 1] >= lo holds
+        // the first task at or after lo, if it has one, else a later slice does.
+        int x = 0, y = S;
+        while (x < y) {
+            const int m = (x + y) >> 1;
+            if (base[m + 1] < lo) x = m + 1; else y = m;
+        }
+        s = x;
+        t = 0;
+        if (s < S) {
+            const int32_t* cls = (rows_side ? om.rcls : om.ccls) + (int64_t)s * 16;
+            const int32_t* tb = (rows_side ? om.rtb : om.ctb) + (int64_t)s * om.tcap;
+            int a = 0, b = cls[8 + kClasses];
+            while (a < b) {
+                const int m = (a + b) >> 1;
+                if (base[s] + tb[m] < lo) a = m + 1; else b = m;
+            }
+            t = a;
+        }
+    }
+    for (;;) {
+        if (threadIdx.x == 0) {
+            // the next slice segment of this CTA: tasks [t, t1) of slice s starting before hi
+            int seg = -1, t0 = 0, t1 = 0;
+            while (s < S) {
+                const int32_t* cls = (rows_side ? om.rcls : om.ccls) + (int64_t)s * 16;
+                const int32_t* tb = (rows_side ? om.rtb : om.ctb) + (int64_t)s * om.tcap;
+                const int T = cls[8 + kClasses];
+                if (t < T && base[s] + tb[t] < hi) {
+                    int x = t, y = T;  // first task at or after hi
+                    while (x < y) {
+                        const int m = (x + y) >> 1;
+                        if (base[s] + tb[m] < hi) x = m + 1; else y = m;
+                    }
+                    seg = s;
+                    t0 = t;
+                    t1 = x;
+                    if (x < T) {
+                        s = S;  // the share ends inside this slice
+                    } else {
+                        ++s;
+                        t = 0;
+                    }
+                    break;
+                }
+                if (t < T) {  // the next task of this slice is past hi: done
+                    s = S;
+                    break;
+                }
+                ++s;
+                t = 0;
+            }
+            s_slice = seg;
+            s_t0 = t0;
+            s_t1 = t1;
+            s_next = t0;
+        }
+        __syncthreads();
+        const int sl = s_slice;
+        if (sl < 0) break;
+        const int row0 = F.slice_off[sl], ms = F.slice_off[sl + 1] - row0, ns = smp.ncol[sl];
+        const float* src = rows_side ? Fin + (int64_t)sl * F.C * r : Fin + (int64_t)row0 * r;
+        const int nsrc = rows_side ? ns : ms;
+        const bool staged = nsrc <= stage_rows;
+        if (staged) stage_factors<RP>(src, nsrc, r, stage4);
+        __syncthreads();
+        const int32_t* ord = rows_side ? om.rord + row0 : om.cord + (int64_t)sl * F.C;
+        const int32_t* cls = (rows_side ? om.rcls : om.ccls) + (int64_t)sl * 16;
+        const int32_t* tb = (rows_side ? om.rtb : om.ctb) + (int64_t)sl * om.tcap;
+        const int t1 = s_t1;
+        for (;;) {
+            int tk = 0;
+            if (lane == 0) tk = atomicAdd(&s_next, 1);
+            tk = __shfl_sync(0xffffffffu, tk, 0);
+            if (tk >= t1) break;
+            int k = 0;
+            while (k + 1 < kClasses && tk >= cls[8 + k + 1]) ++k;
+            const int g = kClasses - 1 - k, G = 1 << g;
+            const int li = cls[k] + (tk - cls[8 + k]) * (32 >> g) + (lane >> g);
+            const bool live = li < cls[k + 1];
+            als_line<RP>(F, om, r, rows_side, src, staged, stage4, Fout, lam_rel, q, sl, live ? ord[li] : -1,
+                         lane & (G - 1), G, base[sl] + tb[tk] + 4 * lane);
+        }
+        __syncthreads();  // the stage is reused by the next segment
+    }
 }
 
 // float64 solve of the queued lines (grid-stride over the device count)
@@ -928,14 +1136,29 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         ctx->plan.entries = E;
     }
     const int64_t mr = std::max(f->max_rows, 1);
+    const int r = uv->r;
     Omega om;
     om.bm_stride = mr * ((C + 31) / 32);
     om.bt_stride = (int64_t)C * ((mr + 31) / 32);
+    om.sell = r <= 16;
+    om.csr = !om.sell;
+    // Sliced layout capacity.  Per slice and side, for lines sorted by count, the
+    // padding of a task is at most the entries of the task before it, rounding to a
+    // multiple of 4 slots adds at most 128 slots per task, and there are at most
+    // n / 32 + E_s / (48 * 32) + 6 tasks: at most E_s (1 + 1/48 + 1/12) + 5 n + L_max
+    // + 5 * 32 * kLaneEntries + 768 slots.  Beyond the capacity the scatter latches
+    // LT_ELIMIT.
+    const int64_t nmax = std::max<int64_t>(mr, C);
+    om.sell_cap = om.sell ? E + E / 32 + E / 16 + (int64_t)S * (5 * nmax + 5 * 32 * kLaneEntries + 1024) : 0;
+    om.tcap = (int)nmax + 8;
+    const size_t e_csr = om.csr ? (size_t)E : 0, e_sell = (size_t)om.sell_cap;
+    const size_t t_sell = om.sell ? (size_t)S * om.tcap : 0;
     lt_status st;
     char* p = (char*)lt_scratch(ctx, SCR_OMEGA,
-                                (size_t)(f->m + S) * 4 + (size_t)S * (C + 1) * 4 + (size_t)E * 12 + S * 8 +
-                                    (size_t)S * (om.bm_stride + om.bt_stride) * 8 + (S + 1) * 8 + (size_t)f->m * 4 +
-                                    (size_t)S * C * 4 + (size_t)S * 128 + 16 * 256,
+                                (size_t)(f->m + S) * 4 + (size_t)S * (C + 1) * 4 + e_csr * 12 + e_sell * 12 + S * 8 +
+                                    (size_t)S * (om.bm_stride + om.bt_stride) * 8 + (S + 1) * 8 + (size_t)f->m * 8 +
+                                    (size_t)S * C * 8 + (size_t)S * 128 + t_sell * 8 + (size_t)(S + 1) * 16 +
+                                    32 * 256,
                                 &st);
     if (!p) return st;
     auto take = [&](size_t nbytes) {
@@ -945,10 +1168,10 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     };
     om.rp = (int32_t*)take((f->m + S) * 4);
     om.cp = (int32_t*)take((size_t)S * (C + 1) * 4);
-    om.cidx = (uint16_t*)take(E * 2);
-    om.cval = (float*)take(E * 4);
-    om.ridx = (uint16_t*)take(E * 2);
-    om.rval = (float*)take(E * 4);
+    om.cidx = (uint16_t*)take(e_csr * 2);
+    om.cval = (float*)take(e_csr * 4);
+    om.ridx = (uint16_t*)take(e_csr * 2);
+    om.rval = (float*)take(e_csr * 4);
     om.mu = (float*)take(S * 4);
     om.bm = (uint32_t*)take((size_t)S * om.bm_stride * 4);
     om.bt = (uint32_t*)take((size_t)S * om.bt_stride * 4);
@@ -959,7 +1182,18 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.cord = (int32_t*)take((size_t)S * C * 4);
     om.rcls = (int32_t*)take((size_t)S * 16 * 4);
     om.ccls = (int32_t*)take((size_t)S * 16 * 4);
-    const int r = uv->r;
+    om.rpos = (int32_t*)take((size_t)f->m * 4);
+    om.cpos = (int32_t*)take((size_t)S * C * 4);
+    om.rtb = (int32_t*)take(t_sell * 4);
+    om.ctb = (int32_t*)take(t_sell * 4);
+    om.rbase = (int64_t*)take((size_t)(S + 1) * 8);
+    om.cbase = (int64_t*)take((size_t)(S + 1) * 8);
+    om.sidx_r = (uint16_t*)take(e_sell * 2);
+    om.sval_r = (float*)take(e_sell * 4);
+    om.sidx_c = (uint16_t*)take(e_sell * 2);
+    om.sval_c = (float*)take(e_sell * 4);
+    if ((size_t)(p - (char*)ctx->scr[SCR_OMEGA]) > ctx->scr_size[SCR_OMEGA])
+        return lt_fail(ctx, LT_ENOMEM, "lt_complete: Omega layout overflow");
     const int RP = r <= 8 ? 8 : r <= 16 ? 16 : 32;
     // per half-step retry counters, the float64 count, the mean partials
     constexpr int kOmParts = 8;
@@ -979,6 +1213,10 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     LT_LAUNCH_CHECK(ctx, "k_om_lines");
     k_om_scan<<<S, 1024, 0, ctx->stream>>>(*f, *smp, om, part, kOmParts);
     LT_LAUNCH_CHECK(ctx, "k_om_scan");
+    if (om.sell) {
+        k_om_sellpfx<<<1, 1024, 0, ctx->stream>>>(S, om, ctx->d_status);
+        LT_LAUNCH_CHECK(ctx, "k_om_sellpfx");
+    }
     k_om_scatter<<<dim3(std::max(1, 4 * nsm / S), S), 256, 0, ctx->stream>>>(*f, *smp, om);
     LT_LAUNCH_CHECK(ctx, "k_om_scatter");
     k_line_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, S, om.line_pfx);
@@ -1009,7 +1247,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
                     AlsQueue<8> q{cnt, qdst, qgram, cap, ctx->d_status};
                     LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)dyn));
-                    k_als_line<8><<<dim3(gx, S), 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout, lam_rel,
+                    k_als_line<8><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout, lam_rel,
                                                                           q, stage_rows);
                     LT_LAUNCH_CHECK(ctx, "k_als_line");
                     k_als_retry<8><<<2 * nsm, 64, 0, ctx->stream>>>(q, r, lam_rel, fout, n64);
@@ -1018,7 +1256,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
                     AlsQueue<16> q{cnt, qdst, qgram, cap, ctx->d_status};
                     LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)dyn));
-                    k_als_line<16><<<dim3(gx, S), 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout,
+                    k_als_line<16><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout,
                                                                            lam_rel, q, stage_rows);
                     LT_LAUNCH_CHECK(ctx, "k_als_line");
                     k_als_retry<16><<<2 * nsm, 64, 0, ctx->stream>>>(q, r, lam_rel, fout, n64);
