@@ -23,6 +23,9 @@ for Light Transport in VPL-based Rendering"):
               factor form M = X Y, rank q)
   render      the image from the factors, X (Y e) (Sec. 3 step 5)
   pipeline    the five steps end to end
+  proposal    the learned pass-2 proposal (an extension the paper leaves to future
+              work): features, leverage targets, the bfloat16 MLP, its gradients
+              and Adam
 
 Every readings of a passage that the paper leaves open is stated in the docstring
 of the function that takes it.
