@@ -219,6 +219,60 @@ lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int
 lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
                     const float* w, const int32_t* row_perm, float* img);
 
+/* ---- Learned pass-2 proposal ---------------------------------------------
+ * The paper draws pass-2 columns from the pass-1 estimate g (Sec. 5) and leaves a
+ * learned importance to future work; these calls are that extension.  Rows of the
+ * proposal are the (slice, coarsened column) pairs, compacted: row group_off[s] + j
+ * for column j < ncol[s] of slice s (group_off[S] rows in all).
+ * Features (32 floats per row): mean position and mean normal of the slice's points,
+ * the slice's AABB, the AABB of the column's tree node, position and normal of its
+ * representative VPL, log(I_c / I_root), mean / std / log(1 + count) / min / max of
+ * the column's pass-1 values (values divided by the slice's mean pass-1 value),
+ * log(m') / 10 and log(n') / 10.
+ * Network: 32 -> 64 -> 64 -> 64 -> 1 with SiLU; theta[LT_MLP_PARAMS] is the float32
+ * master copy laid out W1[64][32] b1[64] W2[64][64] b2[64] W3[64][64] b3[64] W4[64]
+ * b4; the kernels round weights, inputs and hidden activations to bfloat16 (nearest
+ * even) and accumulate in float32 on the tensor cores. */
+#define LT_MLP_FEATURES 32
+#define LT_MLP_HIDDEN 64
+#define LT_MLP_PARAMS 10497
+
+/* Features of every row after lt_sample_pass1: feat[S*C][32] (capacity; rows beyond
+ * group_off[S] untouched), group_off[S+1] written. */
+lt_status lt_proposal_features(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, float* feat,
+                               int32_t* group_off);
+/* Logits z[n] of the network on feat[n][32]; n = min(n_max, *n_dev) when n_dev (a
+ * device int32) is given, else n_max. */
+lt_status lt_proposal_forward(lt_ctx* ctx, const float* theta, const float* feat, int64_t n_max,
+                              const int32_t* n_dev, float* z);
+/* Pass-2 column weights w[S][C] = mix softmax_s(z)_j + (1 - mix) g_j / sum_j g_j,
+ * z in row order (softmax over each slice's rows), 0 <= mix <= 1. */
+lt_status lt_proposal_weights(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const int32_t* group_off,
+                              const float* z, float mix, float* w);
+/* Training data: the full matrix of every slice over its coarsened columns,
+ * M_s[i][j] = A(row i of s, column j) row-major at M + moff[s] (moff[S+1] written);
+ * a total beyond cap floats latches LT_ELIMIT and writes nothing. */
+lt_status lt_slice_matrices(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, float d_min, float* M,
+                            int64_t cap, int64_t* moff);
+/* Training targets, in row order: p_j = (l_j + 1/n') / sum, l_j the squared norm of
+ * row j of the basis after `iters` rounds of subspace iteration Q <- mgs(M^T M Q)
+ * (modified Gram-Schmidt) from a Philox start (counter (k, j, slice, 4)), rank
+ * min(r, n').  Slices with n' > 4096 are skipped. */
+lt_status lt_leverage_targets(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const float* M,
+                              const int64_t* moff, const int32_t* group_off, int32_t r, int32_t iters,
+                              uint64_t seed, float* target);
+/* theta = weights uniform in +-1/sqrt(fan_in) from Philox (counter (p, 0, 0, 5)), biases 0. */
+lt_status lt_proposal_init(lt_ctx* ctx, uint64_t seed, float* theta);
+/* Gradient grad[LT_MLP_PARAMS] of the mean over the ngroups groups (rows
+ * group_off[g] .. group_off[g+1]) of the cross-entropy between target and the
+ * group softmax of the logits, over n rows; the loss goes to the device float *loss
+ * (may be NULL).  Deterministic (fixed reduction order). */
+lt_status lt_proposal_grad(lt_ctx* ctx, const float* theta, const float* feat, const float* target,
+                           const int32_t* group_off, int32_t ngroups, int64_t n, float* grad, float* loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected with `step` >= 1). */
+lt_status lt_proposal_adam(lt_ctx* ctx, float* theta, float* m, float* v, const float* grad, int32_t step,
+                           float lr);
+
 /* ---- The whole frame (Sec. 3 steps 3-5) ----------------------------------- */
 /* Parameters of one frame. */
 typedef struct {
@@ -229,6 +283,9 @@ typedef struct {
     int32_t als_iters;    /* ALS sweeps */
     float lam_rel;        /* ALS ridge, relative to trace(G)/r */
     const float* weights; /* pass-2 column weights [S][C]; NULL = the pass-1 estimate g (Sec. 5) */
+    const float* proposal;/* theta of the learned proposal; when given (and weights is NULL)
+                             pass 2 draws from its weights with mixing factor `mix` */
+    float mix;
 } lt_params;
 
 /* One frame as a sequence of launches on the context's stream: lt_sample_pass1,

@@ -24,14 +24,33 @@ __global__ void k_set_seed(uint64_t* dst, uint64_t seed) { *dst = seed; }
 
 bool params_ok(const lt_params* p) {
     return p && p->rate1 >= 0.f && p->tau >= 0.f && p->d_min >= 0.f && p->rate >= 0.f && p->als_iters >= 0 &&
-           p->lam_rel >= 0.f;
+           p->lam_rel >= 0.f && (!p->proposal || (p->mix >= 0.f && p->mix <= 1.f));
 }
 
 lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed, lt_samples* smp,
                     lt_factors* uv, const int32_t* row_perm, float* img) {
     lt_status st = lt_sample_pass1(ctx, f, p->rate1, p->tau, p->d_min, seed, smp);
     if (st != LT_OK) return st;
-    st = lt_sample_pass2(ctx, f, p->weights, p->rate, seed, smp);
+    const float* w = p->weights;
+    if (!w && p->proposal) {
+        // learned proposal: features -> logits -> mixed weights, all on the stream
+        const size_t rows = (size_t)f->S * f->C;
+        char* q = (char*)lt_scratch(ctx, SCR_FRAME_PROP, rows * (LT_MLP_FEATURES + 2) * 4 + (f->S + 1) * 4 + 4 * 256,
+                                    &st);
+        if (!q) return st;
+        float* feat = (float*)q;
+        float* z = feat + rows * LT_MLP_FEATURES;
+        float* wts = z + rows;
+        int32_t* goff = (int32_t*)((char*)(wts + rows) + 256 - (((size_t)(wts + rows)) & 255));
+        st = lt_proposal_features(ctx, f, smp, feat, goff);
+        if (st != LT_OK) return st;
+        st = lt_proposal_forward(ctx, p->proposal, feat, (int64_t)rows, goff + f->S, z);
+        if (st != LT_OK) return st;
+        st = lt_proposal_weights(ctx, f, smp, goff, z, p->mix, wts);
+        if (st != LT_OK) return st;
+        w = wts;
+    }
+    st = lt_sample_pass2(ctx, f, w, p->rate, seed, smp);
     if (st != LT_OK) return st;
     st = lt_eval_entries(ctx, f, p->d_min, smp);
     if (st != LT_OK) return st;

@@ -359,6 +359,10 @@ enum ScratchSlot {
     SCR_SORT,           // sort keys
     SCR_CUT,            // global-cut work arrays
     SCR_GRAM,           // per-line Gram matrices of an ALS half-step
+    SCR_PROPOSAL,       // per-slice feature statistics
+    SCR_PROPOSAL_T,     // Gram matrices and subspace bases of the targets
+    SCR_PROPOSAL_G,     // logits, their gradient and per-CTA weight gradients
+    SCR_FRAME_PROP,     // features, groups, logits and weights of a frame's proposal
     SCR_NSLOTS
 };
 

@@ -57,7 +57,10 @@ class lt_factors(ctypes.Structure):
 
 class lt_params(ctypes.Structure):
     _fields_ = [("rate1", _f32), ("tau", _f32), ("d_min", _f32), ("rate", _f32), ("als_iters", _i32),
-                ("lam_rel", _f32), ("weights", _p)]
+                ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32)]
+
+
+MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 32, 64, 10497
 
 
 _SIGS = {
@@ -94,6 +97,15 @@ _SIGS = {
                                       ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p, _p,
                                       ctypes.POINTER(_p)]),
     "lt_frame_graph_launch": (_i32, [_p, _u64]),
+    "lt_proposal_features": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _p, _p]),
+    "lt_proposal_forward": (_i32, [_p, _p, _p, _i64, _p, _p]),
+    "lt_proposal_weights": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _p, _p, _f32, _p]),
+    "lt_slice_matrices": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _f32, _p, _i64, _p]),
+    "lt_leverage_targets": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _p, _p, _p, _i32, _i32,
+                                   _u64, _p]),
+    "lt_proposal_init": (_i32, [_p, _u64, _p]),
+    "lt_proposal_grad": (_i32, [_p, _p, _p, _p, _p, _i32, _i64, _p, _p]),
+    "lt_proposal_adam": (_i32, [_p, _p, _p, _p, _p, _i32, _f32]),
     "lt_frame_graph_kernels": (_i64, [_p]),
     "lt_frame_graph_destroy": (_i32, [_p]),
 }
@@ -383,10 +395,10 @@ def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, i
                                               ctypes.byref(uv.struct()), _ptr(w), _ptr(row_perm), _ptr(img)))
 
 
-def params(cfg: dict, weights=None) -> lt_params:
+def params(cfg: dict, weights=None, proposal=None, mix: float = 0.8) -> lt_params:
     """lt_params of a configuration dict (rate1, tau, d_min, rate, als_iters, lam_rel)."""
     return lt_params(cfg["rate1"], cfg["tau"], cfg["d_min"], cfg["rate"], cfg["als_iters"], cfg["lam_rel"],
-                     _ptr(weights))
+                     _ptr(weights), _ptr(proposal), mix)
 
 
 def lt_render_frame(ctx: Context, frame: Frame, prm: lt_params, seed, smp: Samples, uv: Factors, row_perm, img):
@@ -437,3 +449,78 @@ def lt_frame_graph_kernels(g: Graph) -> int:
 
 def lt_frame_graph_destroy(g: Graph):
     g.close()
+
+
+# ------------------------------------------------------------------ learned proposal
+def lt_proposal_features(ctx: Context, frame: Frame, smp: Samples, feat=None, group_off=None):
+    """(feat [S*C][32] float32, group_off [S+1] int32) after pass 1."""
+    dev = frame.pts_s.device
+    if feat is None:
+        feat = torch.zeros(frame.S * frame.C, MLP_FEATURES, dtype=torch.float32, device=dev)
+    if group_off is None:
+        group_off = torch.zeros(frame.S + 1, dtype=torch.int32, device=dev)
+    ctx._check("lt_proposal_features", ctx.lib.lt_proposal_features(ctx.h, ctypes.byref(frame.struct()),
+                                                                    ctypes.byref(smp.struct()), _ptr(feat),
+                                                                    _ptr(group_off)))
+    return feat, group_off
+
+
+def lt_proposal_forward(ctx: Context, theta, feat, n_max=None, n_dev=None, z=None):
+    n_max = feat.shape[0] if n_max is None else n_max
+    if z is None:
+        z = torch.zeros(n_max, dtype=torch.float32, device=feat.device)
+    ctx._check("lt_proposal_forward", ctx.lib.lt_proposal_forward(ctx.h, _ptr(theta), _ptr(feat), n_max, _ptr(n_dev),
+                                                                  _ptr(z)))
+    return z
+
+
+def lt_proposal_weights(ctx: Context, frame: Frame, smp: Samples, group_off, z, mix=0.8, w=None):
+    if w is None:
+        w = torch.zeros(frame.S * frame.C, dtype=torch.float32, device=z.device)
+    ctx._check("lt_proposal_weights", ctx.lib.lt_proposal_weights(ctx.h, ctypes.byref(frame.struct()),
+                                                                  ctypes.byref(smp.struct()), _ptr(group_off),
+                                                                  _ptr(z), mix, _ptr(w)))
+    return w
+
+
+def lt_slice_matrices(ctx: Context, frame: Frame, smp: Samples, d_min, cap: int):
+    """(M [cap] float32, moff [S+1] int64): the full matrix of every slice over its coarsened columns."""
+    dev = frame.pts_s.device
+    M = torch.zeros(max(int(cap), 1), dtype=torch.float32, device=dev)
+    moff = torch.zeros(frame.S + 1, dtype=torch.int64, device=dev)
+    ctx._check("lt_slice_matrices", ctx.lib.lt_slice_matrices(ctx.h, ctypes.byref(frame.struct()),
+                                                              ctypes.byref(smp.struct()), d_min, _ptr(M), int(cap),
+                                                              _ptr(moff)))
+    return M, moff
+
+
+def lt_leverage_targets(ctx: Context, frame: Frame, smp: Samples, M, moff, group_off, r, iters, seed, target=None):
+    if target is None:
+        target = torch.zeros(frame.S * frame.C, dtype=torch.float32, device=M.device)
+    ctx._check("lt_leverage_targets", ctx.lib.lt_leverage_targets(ctx.h, ctypes.byref(frame.struct()),
+                                                                  ctypes.byref(smp.struct()), _ptr(M), _ptr(moff),
+                                                                  _ptr(group_off), r, iters, seed, _ptr(target)))
+    return target
+
+
+def lt_proposal_init(ctx: Context, seed, device=None):
+    device = torch.device("cuda", ctx.device) if device is None else device
+    theta = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=device)
+    ctx._check("lt_proposal_init", ctx.lib.lt_proposal_init(ctx.h, seed, _ptr(theta)))
+    return theta
+
+
+def lt_proposal_grad(ctx: Context, theta, feat, target, group_off, ngroups, n, grad=None, loss=None):
+    if grad is None:
+        grad = torch.zeros(MLP_PARAMS, dtype=torch.float32, device=theta.device)
+    if loss is None:
+        loss = torch.zeros(1, dtype=torch.float32, device=theta.device)
+    ctx._check("lt_proposal_grad", ctx.lib.lt_proposal_grad(ctx.h, _ptr(theta), _ptr(feat), _ptr(target),
+                                                            _ptr(group_off), int(ngroups), int(n), _ptr(grad),
+                                                            _ptr(loss)))
+    return grad, loss
+
+
+def lt_proposal_adam(ctx: Context, theta, m, v, grad, step, lr):
+    ctx._check("lt_proposal_adam", ctx.lib.lt_proposal_adam(ctx.h, _ptr(theta), _ptr(m), _ptr(v), _ptr(grad),
+                                                            int(step), lr))
