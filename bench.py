@@ -3,7 +3,11 @@
 A step is one frame of the method's hot path (pass 1 + coarsening, pass 2, entry
 evaluation, masked-ALS completion of every slice, factorised render) on the
 256x256-point, 16384-VPL room scene with two boxes (the scene family of the
-learned-proposal experiments), 64 slices, 15% sampling, rank 16.
+learned-proposal experiments, held-out seed 5000), 64 slices, 15% sampling, rank 16.
+The timed form is the batched one with the learned proposal: the whole frame is one
+captured CUDA graph and pass 2 draws from the shipped network's weights mixed with
+g.  Next to it: the same graph with the paper's pdf g, the plain form (the same
+calls one by one, with their host synchronisations) and the brute-force sum.
 Setup (light tree, global cut, slices) is timed separately and reported.  Quality
 is the rel-RMSE of the frame against the brute-force column sum over all VPLs
 (computed on the GPU by the library's brute-force kernel, which the tests check
@@ -162,6 +166,29 @@ def eval_roofline(lt, ctx, R, stage_ms, clk):
                           ops_per_launch=int(ops)))
 
 
+# DRAM bytes per ALS half-step launch (U-step 40,988,160, V-step 42,793,472; mean),
+# from the ncu capture in profiles/k_als_line_room256_vpl16k_2box.md of this kernel
+ALS_TRAFFIC_BYTES = 41_890_816
+
+
+def als_roofline(lt, ctx, R, half_ms):
+    """FP32 roofline of the lane-group ALS half-step (k_als_line): per observed entry
+    r(r+1)/2 + r FMAs (Gram lower triangle and right-hand side), per line a Cholesky
+    (r^3/3 flops) and two triangular solves (2 r^2 flops)."""
+    r = R.cfg["rank"]
+    E = int(R.smp.cnt.sum())
+    lines = (R.frame.m + int(R.smp.ncol.sum())) / 2.0
+    flops = 2.0 * E * (r * (r + 1) / 2 + r) + lines * (r ** 3 / 3.0 + 2.0 * r * r)
+    achieved = flops / (half_ms * 1e-3) / 1e12
+    peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    return dict(bound="alu", kernel="k_als_line (ALS half-step)", achieved=round(achieved, 3), peak=round(peak, 2),
+                unit="TFLOP/s", frac=round(achieved / peak, 4),
+                traffic=ALS_TRAFFIC_BYTES if R.cfg["rank"] == 16 else None,
+                peak_source="152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max SM clock (derived)",
+                launch_ms=round(half_ms, 4),
+                work=dict(entries=E, lines_per_half_step=lines, flops_per_launch=int(flops)))
+
+
 # ------------------------------------------------------------------ GPU leg
 def run_ours(args):
     import numpy as np
@@ -218,29 +245,45 @@ def run_ours(args):
         if ev:
             ev[5].record()
 
+    from paper_2202_12567_gb300 import proposal
+    theta = proposal.load_theta(device=local) if os.path.exists(proposal.DEFAULT_THETA) else None
+
     for i in range(args.warmup):
         frame(i)
     lt.lt_sync(ctx)
-    graph = R.capture()  # the batched form: the whole frame as one CUDA graph
+    # the batched form: the whole frame as one CUDA graph, pass 2 from the learned
+    # proposal (or from g when no trained network is shipped)
+    prm_g = lt.params(cfg)
+    graph_g = lt.lt_frame_graph_capture(ctx, R.frame, prm_g, R.smp, R.uv, R.row_perm, R.img)
+    if theta is not None:
+        prm_l = lt.params(cfg, proposal=theta, mix=0.8)
+        graph = lt.lt_frame_graph_capture(ctx, R.frame, prm_l, R.smp, R.uv, R.row_perm, R.img, keep=(theta,))
+    else:
+        graph = graph_g
     for i in range(args.warmup):
-        R.render_graph(seed0 + 100 + i, sync=False)
+        lt.lt_frame_graph_launch(graph, seed0 + 100 + i)
+        lt.lt_frame_graph_launch(graph_g, seed0 + 100 + i)
     lt.lt_sync(ctx)
+
+    def replay(g, k0):
+        ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            lt.lt_frame_graph_launch(g, seed0 + k0 + k)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return ms
 
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    launches0 = lt.lt_launch_count(ctx)
     clocks = ClockSampler(local)
-    per = []
-    for k in range(args.steps):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        R.render_graph(seed0 + 1000 + k, sync=False)
-        b.record()
-        torch.cuda.synchronize()
-        per.append(a.elapsed_time(b))
+    launches0 = lt.lt_launch_count(ctx)
+    per = replay(graph, 1000)
     torch.cuda.synchronize()
     launches = lt.lt_launch_count(ctx) - launches0
     lt.lt_sync(ctx)
@@ -251,7 +294,11 @@ def run_ours(args):
         total_ms = float(t.item())
         dist.barrier()
     ms_frame = total_ms / (args.steps * world)
-    img_graph = R.img.clone()
+    img = R.img.clone()
+    # the same graph with the paper's pdf g (seeds as above: the same pass-1 draws)
+    per_g = replay(graph_g, 1000)
+    img_g = R.img.clone()
+    g_graph_ms = statistics.mean(per_g)
 
     # the plain form (the same calls one by one, with the two size read-backs),
     # with events between the stages for the breakdown
@@ -264,14 +311,27 @@ def run_ours(args):
         torch.cuda.synchronize()
         plain.append(evs[0].elapsed_time(evs[5]))
         stage_ms += np.array([evs[j].elapsed_time(evs[j + 1]) for j in range(5)])
-    clk = clocks.stop()
-    lt.lt_sync(ctx)
     stage_ms /= args.steps
     plain_ms = statistics.mean(plain)
-    same_as_graph = bool(torch.equal(R.img, img_graph))
+    same_as_graph = bool(torch.equal(R.img, img_g))
+    # ALS half-step on the launching stream: complete at K sweeps minus at 0 sweeps
+    c_ms = {}
+    for iters in (cfg["als_iters"], 0):
+        xs = []
+        for k in range(max(3, args.steps // 4)):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            lt.lt_complete(ctx, R.frame, R.smp, R.uv, iters, cfg["lam_rel"], seed0)
+            b.record()
+            torch.cuda.synchronize()
+            xs.append(a.elapsed_time(b))
+        c_ms[iters] = statistics.median(xs[1:])
+    half_ms = (c_ms[cfg["als_iters"]] - c_ms[0]) / (2 * cfg["als_iters"])
+    clk = clocks.stop()
+    lt.lt_sync(ctx)
 
-    # quality: the last frame against the brute-force column sum over all VPLs
-    img = R.img.clone()
+    # quality: the last frames against the brute-force column sum over all VPLs
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     bf = torch.empty_like(img)
@@ -282,7 +342,9 @@ def run_ours(args):
     e1.record()
     torch.cuda.synchronize()
     bf_ms = e0.elapsed_time(e1)
-    rel = float(torch.linalg.norm(img.double() - bf.double()) / torch.linalg.norm(bf.double()))
+    nbf = torch.linalg.norm(bf.double())
+    rel = float(torch.linalg.norm(img.double() - bf.double()) / nbf)
+    rel_g = float(torch.linalg.norm(img_g.double() - bf.double()) / nbf)
     rays_per_px = float(R.rays()) / R.frame.m
 
     # end to end through the C ABI from pinned host buffers: points and VPLs in, image out
@@ -299,7 +361,7 @@ def run_ours(args):
         R.pts.copy_(pts_h, non_blocking=True)
         R.vpls.copy_(vpl_h, non_blocking=True)
         R.pts_s.copy_(lt.lt_permute_points(ctx, R.pts, R.row_perm))
-        R.render_graph(seed0 + 5000 + k, sync=False)
+        lt.lt_frame_graph_launch(graph, seed0 + 5000 + k)
         img_h.copy_(R.img, non_blocking=True)
         b.record()
         torch.cuda.synchronize()
@@ -309,7 +371,8 @@ def run_ours(args):
     h2d = sc.points.nbytes + sc.vpls.nbytes
     d2h = img_h.numel() * 4
 
-    roof = eval_roofline(lt, ctx, R, stage_ms, clk)
+    roof = als_roofline(lt, ctx, R, half_ms)
+    roof_eval = eval_roofline(lt, ctx, R, stage_ms, clk)
 
     line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
@@ -320,10 +383,15 @@ def run_ours(args):
                             l2="flushed (256 MB write) between timed frames", global_cut=int(R.frame.C),
                             rel_rmse_vs_bruteforce=round(rel, 5), rays_per_pixel=round(rays_per_px, 2),
                             bruteforce_gpu_ms=round(bf_ms, 3), speedup_vs_bruteforce=round(bf_ms / ms_frame, 2),
-                            form="batched: the frame as one captured CUDA graph, "
-                                 f"{graph.kernels} kernels per replay",
+                            form=("batched + learned proposal: the frame as one captured CUDA graph "
+                                  f"({graph.kernels} kernels per replay), pass 2 from 0.8 softmax(MLP) + 0.2 g"
+                                  if theta is not None else
+                                  f"batched: the frame as one captured CUDA graph ({graph.kernels} kernels)"),
+                            paper_pdf_graph_ms=round(g_graph_ms, 4),
+                            rel_rmse_paper_pdf=round(rel_g, 5),
                             plain_form_ms=round(plain_ms, 4), speedup_vs_plain_form=round(plain_ms / ms_frame, 3),
                             plain_equals_graph_bitwise=same_as_graph,
+                            eval_roofline=roof_eval,
                             setup_ms=round(setup_ms, 1),
                             stage_ms=dict(zip(["pass1", "pass2", "eval", "complete", "render"],
                                               [round(x, 4) for x in stage_ms.tolist()]))),

@@ -214,3 +214,20 @@ def test_frame_with_proposal_replays_and_keeps_the_sample_count(lt):
     lt.lt_sync(R.ctx)
     assert torch.equal(R.img, img)
     g.close()
+
+
+def test_shipped_proposal_beats_g_at_equal_sample_count(lt):
+    """The network trained by `python -m paper_2202_12567_gb300.proposal` (200 scenes
+    1000..1199) against the paper's pdf g on held-out scenes of the same generator."""
+    import os
+    from paper_2202_12567_gb300 import proposal
+    if not os.path.exists(proposal.DEFAULT_THETA):
+        pytest.skip("no trained proposal shipped")
+    cfg = get_config("room256_vpl16k_2box")
+    ctx = lt.Context(0)
+    theta = proposal.load_theta()
+    res = proposal.ab_compare(ctx, cfg, theta, [5001, 5002, 5003])
+    assert all(r["entries_g"] == r["entries_learned"] for r in res)
+    g = np.mean([r["rel_g"] for r in res])
+    p = np.mean([r["rel_learned"] for r in res])
+    assert p < g, res
