@@ -166,8 +166,9 @@ def eval_roofline(lt, ctx, R, stage_ms, clk):
                           ops_per_launch=int(ops)))
 
 
-# DRAM bytes per ALS half-step launch (U-step 40,988,160, V-step 42,793,472; mean),
-# from the ncu capture in profiles/k_als_line_room256_vpl16k_2box.md of this kernel
+# DRAM bytes per ALS half-step launch on this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture of k_als_line<16>: U-step 40,988,160,
+# V-step 42,793,472; their mean)
 ALS_TRAFFIC_BYTES = 41_890_816
 
 
