@@ -290,9 +290,8 @@ def run_ours(args):
     lt.lt_sync(ctx)
     total_ms = float(sum(per))
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_2202_12567_gb300 import shard
+        total_ms = shard.max_over_ranks(total_ms, device=dev)
         dist.barrier()
     ms_frame = total_ms / (args.steps * world)
     img = R.img.clone()

@@ -1,0 +1,84 @@
+"""One frame over several processes (one GPU each), sharded by slices.
+
+Slices are independent after setup (Sec. 3: every slice is sampled and completed on
+its own), so a frame shards with no exchange on the data path: the slices are split
+by longest-processing-time on their estimated cost, every rank renders its slices,
+and the pixel blocks are gathered once at the end.  The functions here are the
+host side of that split; they run on any torch.distributed backend (gloo on CPU,
+NCCL between GPUs).
+"""
+from __future__ import annotations
+
+import heapq
+
+import numpy as np
+import torch
+import torch.distributed as dist
+
+
+def slice_costs(slice_off, ncol=None, C: int | None = None) -> np.ndarray:
+    """Estimated cost of each slice: m'_s n'_s entries to sample and complete (the
+    global cut size C stands in for n'_s before pass 1)."""
+    sizes = np.diff(np.asarray(slice_off, dtype=np.int64))
+    n = np.asarray(ncol, dtype=np.int64) if ncol is not None else np.full(sizes.size, int(C or 1))
+    return sizes * np.maximum(n, 1)
+
+
+def lpt_partition(costs, world: int):
+    """Slices per rank: largest cost first onto the least-loaded rank (ties: lower
+    slice index, lower rank).  Returns sorted slice lists."""
+    order = sorted(range(len(costs)), key=lambda s: (-int(costs[s]), s))
+    heap = [(0, r) for r in range(world)]
+    out = [[] for _ in range(world)]
+    for s in order:
+        load, r = heapq.heappop(heap)
+        out[r].append(s)
+        heapq.heappush(heap, (load + int(costs[s]), r))
+    return [sorted(x) for x in out]
+
+
+def rows_of(slice_off, slices) -> np.ndarray:
+    """Slice-ordered rows of the given slices."""
+    off = np.asarray(slice_off, dtype=np.int64)
+    if len(slices) == 0:
+        return np.zeros(0, dtype=np.int64)
+    return np.concatenate([np.arange(off[s], off[s + 1]) for s in slices])
+
+
+def gather_image(pixels: torch.Tensor, values: torch.Tensor, m: int, dst: int = 0, group=None):
+    """Every rank holds values at pixel indices; rank `dst` returns the full image
+    [m] (other ranks None).  Blocks of different sizes are padded to the largest."""
+    world = dist.get_world_size(group)
+    n = torch.tensor([pixels.numel()], dtype=torch.int64)
+    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(sizes, n, group=group)
+    cap = int(max(int(x.item()) for x in sizes))
+    pad_p = torch.full((cap,), -1, dtype=torch.int64)
+    pad_v = torch.zeros(cap, dtype=values.dtype)
+    pad_p[:pixels.numel()] = pixels.to(torch.int64).cpu()
+    pad_v[:values.numel()] = values.cpu()
+    all_p = [torch.empty(cap, dtype=torch.int64) for _ in range(world)]
+    all_v = [torch.empty(cap, dtype=values.dtype) for _ in range(world)]
+    dist.all_gather(all_p, pad_p, group=group)
+    dist.all_gather(all_v, pad_v, group=group)
+    if dist.get_rank(group) != dst:
+        return None
+    img = torch.zeros(m, dtype=values.dtype)
+    seen = torch.zeros(m, dtype=torch.bool)
+    for p, v, k in zip(all_p, all_v, sizes):
+        k = int(k.item())
+        p, v = p[:k], v[:k]
+        if bool(seen[p].any()):
+            raise RuntimeError("a pixel was rendered by two ranks")
+        img[p] = v
+        seen[p] = True
+    if not bool(seen.all()):
+        raise RuntimeError("pixels missing from the gathered image")
+    return img
+
+
+def max_over_ranks(x: float, group=None, device=None) -> float:
+    """The largest value over the ranks (the frame time of a sharded run)."""
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
