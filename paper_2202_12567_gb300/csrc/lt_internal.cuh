@@ -363,6 +363,7 @@ enum ScratchSlot {
     SCR_PROPOSAL_T,     // Gram matrices and subspace bases of the targets
     SCR_PROPOSAL_G,     // logits, their gradient and per-CTA weight gradients
     SCR_FRAME_PROP,     // features, groups, logits and weights of a frame's proposal
+    SCR_P2_CDF,         // pass-2 integer CDF of every slice
     SCR_NSLOTS
 };
 

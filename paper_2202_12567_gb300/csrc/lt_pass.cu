@@ -10,6 +10,7 @@
 //    of g, row uniform) in blocks of blockDim draws, keeps the first occurrence of
 //    every new entry in draw order, and stops at ceil(rate m' n') entries.
 //  * Entry evaluation: one thread per pass-2 entry (one shadow ray).
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <algorithm>
@@ -384,62 +385,78 @@ __global__ void k_p1_setup(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h, i
     }
 }
 
-// the same for pairs with more than kThreadPair rows, one warp per pair
-__global__ void k_p1_setup_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h, int32_t* status) {
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
+// the same for pairs with more than kThreadPair rows, one CTA per pair: both sorted
+// row lists staged in shared memory (global reads beyond kBigStage rows), the union
+// slot of a row = its index + its rank in the other list - the common rows before it
+// (a block scan of the "in both" flags)
+constexpr int kBigStage = 4096;
+
+__global__ void __launch_bounds__(256) k_p1_setup_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h,
+                                                      int32_t* status) {
+    __shared__ int32_t sa[kBigStage], sb[kBigStage];
+    __shared__ int32_t ws[32];
     const int NF = 2 * F.C - 1;
     const int64_t nbig = min(w.bcount[h], w.bcap);
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nbig;
-         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t q = blockIdx.x; q < nbig; q += gridDim.x) {
         PairCtx pc;
-        load_pair(F, pl, st, h, w.big[q], pc);
+        if (!load_pair(F, pl, st, h, w.big[q], pc)) continue;  // uniform in the block
         const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b];
+        const bool staged = pc.na <= kBigStage && pc.nb <= kBigStage;
+        __syncthreads();  // the previous pair is done with the stage
+        if (staged) {
+            for (int i = threadIdx.x; i < pc.na; i += blockDim.x) sa[i] = pc.ra[i];
+            for (int j = threadIdx.x; j < pc.nb; j += blockDim.x) sb[j] = pc.rb[j];
+        }
+        __syncthreads();
+        const int32_t* A = staged ? sa : pc.ra;
+        const int32_t* B = staged ? sb : pc.rb;
         int32_t* rf = st.rows + pc.iff;
         float* fa = st.v0 + pc.iff;
         float* fb = st.v1 + pc.iff;
         int common = 0;
-        for (int i0 = 0; i0 < pc.na; i0 += 32) {
-            const int i = i0 + lane;
+        for (int i0 = 0; i0 < pc.na; i0 += blockDim.x) {
+            const int i = i0 + threadIdx.x;
             int x = 0, pb = 0;
             bool both = false;
             if (i < pc.na) {
-                x = pc.ra[i];
-                pb = lower_bound<int32_t>(pc.rb, pc.nb, x);
-                both = pb < pc.nb && pc.rb[pb] == x;
+                x = A[i];
+                pb = lower_bound<int32_t>(B, pc.nb, x);
+                both = pb < pc.nb && B[pb] == x;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, both);
+            int tot;
+            const int pre = block_exclusive_scan<int>(both ? 1 : 0, ws, &tot);
             const long long m = warp_reserve((unsigned long long*)&w.mcount[h], (i < pc.na && !both) ? 1 : 0);
             if (i < pc.na) {
-                const int slot = i + pb - (common + __popc(bal & lt_mask));
+                const int slot = i + pb - (common + pre);
                 rf[slot] = x;
                 fa[slot] = st.v0[pc.ia + i];
                 if (both) fb[slot] = st.v0[pc.ib + pb];
-                else put_missing(w, m, st.total + pc.iff + slot, pc.row0 + x, tb, status);
+                else put_missing(w, m, st.total + pc.iff + slot, pc.row0 + x, tb, status);   // V_b(x)
             }
-            common += __popc(bal);
+            common += tot;
         }
         int seen = 0;
-        for (int j0 = 0; j0 < pc.nb; j0 += 32) {
-            const int j = j0 + lane;
+        for (int j0 = 0; j0 < pc.nb; j0 += blockDim.x) {
+            const int j = j0 + threadIdx.x;
             int y = 0, pa = 0;
             bool both = false;
             if (j < pc.nb) {
-                y = pc.rb[j];
-                pa = lower_bound<int32_t>(pc.ra, pc.na, y);
-                both = pa < pc.na && pc.ra[pa] == y;
+                y = B[j];
+                pa = lower_bound<int32_t>(A, pc.na, y);
+                both = pa < pc.na && A[pa] == y;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, both);
+            int tot;
+            const int pre = block_exclusive_scan<int>(both ? 1 : 0, ws, &tot);
             const long long m = warp_reserve((unsigned long long*)&w.mcount[h], (j < pc.nb && !both) ? 1 : 0);
             if (j < pc.nb && !both) {
-                const int slot = j + pa - (seen + __popc(bal & lt_mask));
+                const int slot = j + pa - (seen + pre);
                 rf[slot] = y;
                 fb[slot] = st.v0[pc.ib + j];
-                put_missing(w, m, pc.iff + slot, pc.row0 + y, ta, status);
+                put_missing(w, m, pc.iff + slot, pc.row0 + y, ta, status);   // V_a(y)
             }
-            seen += __popc(bal);
+            seen += tot;
         }
-        if (lane == 0) pl.cnt[(int64_t)pc.s * NF + pc.f] = pc.na + pc.nb - common;
+        if (threadIdx.x == 0) pl.cnt[(int64_t)pc.s * NF + pc.f] = pc.na + pc.nb - common;
     }
 }
 
@@ -515,18 +532,23 @@ __global__ void k_p1_decide(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) 
     }
 }
 
-__global__ void k_p1_decide_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
-    const int lane = threadIdx.x & 31;
+// big pairs, one CTA per pair
+__global__ void __launch_bounds__(256) k_p1_decide_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+    __shared__ float red[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int NF = 2 * F.C - 1;
     const int64_t nbig = min(w.bcount[h], w.bcap);
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nbig;
-         q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    for (int64_t q = blockIdx.x; q < nbig; q += gridDim.x) {
         PairCtx pc;
-        load_pair(F, pl, st, h, w.big[q], pc);
+        if (!load_pair(F, pl, st, h, w.big[q], pc)) continue;  // uniform in the block
         const int nf = pl.cnt[(int64_t)pc.s * NF + pc.f];
-        const float e = warp_max(pair_eps(F, st, pc, nf, lane, 32));
-        __syncwarp();
-        decide_pair(F, pl, st, w.thr, pc, e, lane, 32, lane == 0);
+        const float e = warp_max(pair_eps(F, st, pc, nf, threadIdx.x, blockDim.x));
+        __syncthreads();  // red is free
+        if (lane == 0) red[wid] = e;
+        __syncthreads();
+        float em = 0.f;
+        for (int k = 0; k < nw; ++k) em = fmaxf(em, red[k]);
+        decide_pair(F, pl, st, w.thr, pc, em, threadIdx.x, blockDim.x, threadIdx.x == 0);
     }
 }
 
@@ -651,54 +673,36 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
     return x;
 }
 
-constexpr int kHashSize = 2 * kP2Threads;
 constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr int kP2Cluster = 8;    // CTAs per slice (one thread-block cluster)
+constexpr int kP2Block = 512;    // threads per CTA
+constexpr int kP2Draws = 4;      // draws per thread per round
+constexpr int kGuide = 2048;     // buckets of the CDF guide table
 
-__global__ void __launch_bounds__(kP2Threads) k_pass2(lt_frame F, const float* __restrict__ weights, float rate,
-                                                      SeedRef sr, lt_samples smp, uint32_t* bitmap_all,
-                                                      int64_t bitmap_stride, int32_t* status) {
-    extern __shared__ unsigned long long cdf[];  // [C]
-    __shared__ uint32_t hkey[kHashSize];
-    __shared__ int32_t htid[kHashSize];
-    __shared__ int32_t ws[32];
+// Per slice (one CTA each): the inclusive integer CDF of the quantised column
+// weights (q = max(1, floor(w / w_max * 2^24)), 0 for w <= 0) and the bitmap of the
+// pass-1 entries.
+__global__ void __launch_bounds__(1024) k_p2_prep(lt_frame F, const float* __restrict__ weights, lt_samples smp,
+                                                  unsigned long long* __restrict__ cdf_all,
+                                                  unsigned long long* __restrict__ total_all, uint32_t* bitmap_all,
+                                                  int64_t bitmap_stride) {
+    __shared__ unsigned long long wsum[32];
     __shared__ float red[32];
-    __shared__ unsigned long long s_total;
     const int s = blockIdx.x;
     const int C = F.C;
     const int ms = F.slice_off[s + 1] - F.slice_off[s];
     const int ns = smp.ncol[s];
     const int n1 = smp.n1[s];
-    const uint64_t seed = sr.get();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (ms == 0 || ns == 0) {
-        if (threadIdx.x == 0) smp.cnt[s] = n1;
-        return;
-    }
-    const int64_t T = (int64_t)ceil((double)rate * (double)ms * (double)ns);
-    int64_t need = T - n1;
-    if (need <= 0) {
-        if (threadIdx.x == 0) smp.cnt[s] = n1;
-        return;
-    }
-    const int64_t capacity = smp.off[s + 1] - smp.off[s];
-    if (n1 + need > capacity) {
-        if (threadIdx.x == 0) latch(status, LT_ELIMIT);
-        need = capacity - n1;
-    }
     const float* w = (weights ? weights : smp.g) + (int64_t)s * C;
-    // quantised weights -> inclusive integer CDF
     float wm = 0.f;
     for (int j = threadIdx.x; j < ns; j += blockDim.x) wm = fmaxf(wm, w[j]);
     wm = warp_max(wm);
     if (lane == 0) red[wid] = wm;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float m = 0.f;
-        for (int i = 0; i < nw; ++i) m = fmaxf(m, red[i]);
-        red[0] = m;
-    }
-    __syncthreads();
-    const float wmax = red[0];
+    float wmax = 0.f;
+    for (int i = 0; i < nw; ++i) wmax = fmaxf(wmax, red[i]);
+    unsigned long long* cdf = cdf_all + (int64_t)s * C;
     unsigned long long carry = 0;
     for (int c0 = 0; c0 < ns; c0 += blockDim.x) {
         const int j = c0 + threadIdx.x;
@@ -716,12 +720,11 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(lt_frame F, const float* _
             }
         }
         unsigned long long tot;
-        const unsigned long long pre = block_exclusive_scan<unsigned long long>(q, (unsigned long long*)hkey, &tot);
+        const unsigned long long pre = block_exclusive_scan<unsigned long long>(q, wsum, &tot);
         if (j < ns) cdf[j] = carry + pre + q;
         carry += tot;
     }
-    if (threadIdx.x == 0) s_total = carry;
-    // bitmap of the observed entries: row-major, W words per row
+    if (threadIdx.x == 0) total_all[s] = carry;
     const int W = (ns + 31) >> 5;
     uint32_t* bm = bitmap_all + (int64_t)s * bitmap_stride;
     for (int64_t i = threadIdx.x; i < (int64_t)ms * W; i += blockDim.x) bm[i] = 0u;
@@ -730,68 +733,178 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(lt_frame F, const float* _
     for (int i = threadIdx.x; i < n1; i += blockDim.x) {
         const uint32_t k = key1[i];
         const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
-        atomicOr(bm + (int64_t)r * W + (c >> 5), 1u << (c & 31));
+        if (r < ms && c < ns) atomicOr(bm + (int64_t)r * W + (c >> 5), 1u << (c & 31));
     }
-    for (int i = threadIdx.x; i < kHashSize; i += blockDim.x) {
+}
+
+// One cluster of kP2Cluster CTAs per slice.  A round takes the next
+// kP2Cluster x kP2Block x kP2Draws draws in order (CTA k the k-th block of them,
+// thread i of a CTA kP2Draws consecutive ones), keeps those whose (row, col) is
+// not observed yet (bitmap) and is the first of its key in the round (a hash table
+// spread over the cluster's shared memory: a key lives in the part of CTA
+// hash & (kP2Cluster - 1) and keeps the smallest draw index), and accepts them in
+// draw order (a prefix over the CTAs' counts) up to the target.  Every CTA of the
+// cluster computes the same accepted count, so all take the same cluster barriers.
+__global__ void __cluster_dims__(kP2Cluster, 1, 1) __launch_bounds__(kP2Block, 2)
+    k_pass2(lt_frame F, float rate, SeedRef sr, lt_samples smp, const unsigned long long* __restrict__ cdf_all,
+            const unsigned long long* __restrict__ total_all, uint32_t* bitmap_all, int64_t bitmap_stride, int hpart,
+            int32_t* status) {
+    namespace cg = cooperative_groups;
+    // dynamic shared memory: cdf[C] (u64), hkey[hpart] (u32), htid[hpart] (int32: the
+    // smallest draw index of the key in the round), guide[kGuide + 1] (int32)
+    extern __shared__ unsigned long long p2sm[];
+    unsigned long long* scdf = p2sm;
+    uint32_t* hkey = reinterpret_cast<uint32_t*>(p2sm + F.C);
+    int32_t* htid = reinterpret_cast<int32_t*>(hkey + hpart);
+    int32_t* guide = htid + hpart;
+    __shared__ int32_t ws[32];
+    __shared__ int32_t s_cnt;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int s = blockIdx.x / kP2Cluster;
+    const int C = F.C;
+    const int ms = F.slice_off[s + 1] - F.slice_off[s];
+    const int ns = smp.ncol[s];
+    const int n1 = smp.n1[s];
+    const uint64_t seed = sr.get();
+    if (ms == 0 || ns == 0) {
+        if (rank == 0 && threadIdx.x == 0) smp.cnt[s] = n1;
+        return;
+    }
+    const int64_t T = (int64_t)ceil((double)rate * (double)ms * (double)ns);
+    int64_t need = T - n1;
+    if (need <= 0) {
+        if (rank == 0 && threadIdx.x == 0) smp.cnt[s] = n1;
+        return;
+    }
+    const int64_t capacity = smp.off[s + 1] - smp.off[s];
+    if (n1 + need > capacity) {
+        if (rank == 0 && threadIdx.x == 0) latch(status, LT_ELIMIT);
+        need = capacity - n1;
+    }
+    const unsigned long long total = total_all[s];
+    const uint32_t th = (uint32_t)(total >> 32), tl = (uint32_t)total;
+    const int W = (ns + 31) >> 5;
+    uint32_t* bm = bitmap_all + (int64_t)s * bitmap_stride;
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) scdf[j] = cdf_all[(int64_t)s * C + j];
+    for (int i = threadIdx.x; i < hpart; i += blockDim.x) {
         hkey[i] = kEmpty;
         htid[i] = 0x7fffffff;
     }
     __syncthreads();
-    const unsigned long long total = s_total;
-    const uint32_t th = (uint32_t)(total >> 32), tl = (uint32_t)total;
+    // guide table: guide[k] = first c with cdf[c] > floor(k total / kGuide); a draw u in
+    // bucket k = floor(u kGuide / total) has its column in [guide[k], guide[k + 1]]
+    for (int k = threadIdx.x; k <= kGuide; k += blockDim.x) {
+        const unsigned long long v = (unsigned long long)k * total / kGuide;
+        int a = 0, b = ns - 1;  // cdf[ns - 1] = total > v for k < kGuide
+        while (a < b) {
+            const int m = (a + b) >> 1;
+            if (scdf[m] > v) b = m;
+            else a = m + 1;
+        }
+        guide[k] = a;
+    }
+    cl.sync();
     const int64_t cap_draws = 64 * T + 64;
     uint32_t* keyout = smp.key + smp.off[s] + n1;
+    const int64_t per_cta = (int64_t)blockDim.x * kP2Draws, per_round = per_cta * kP2Cluster;
     int64_t accepted = 0;
-    for (int64_t t0 = 0; accepted < need && t0 < cap_draws; t0 += blockDim.x) {
-        const int64_t t = t0 + threadIdx.x;
-        bool cand = false;
-        uint32_t key = 0;
-        int hslot = -1;
-        int r = 0, c = 0;
-        if (t < cap_draws) {
-            const U4 x = philox((uint32_t)t, 0u, (uint32_t)s, kTagPass2, seed);
-            const unsigned long long u =
-                (unsigned long long)x.x * th + (((unsigned long long)x.x * tl) >> 32);
-            int lo = 0, hi = ns;  // first c with cdf[c] > u
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (cdf[mid] > u) hi = mid;
-                else lo = mid + 1;
+    for (int64_t t0 = 0; accepted < need && t0 < cap_draws; t0 += per_round) {
+        uint32_t rc[kP2Draws];
+        int home[kP2Draws], slot[kP2Draws], tr[kP2Draws];
+        int64_t tt[kP2Draws];
+        unsigned long long u[kP2Draws];
+        uint32_t wrow[kP2Draws];
+#pragma unroll
+        for (int d = 0; d < kP2Draws; ++d) {  // draw and column search, all draws at once
+            tt[d] = t0 + rank * per_cta + (int64_t)threadIdx.x * kP2Draws + d;
+            const U4 x = philox((uint32_t)tt[d], 0u, (uint32_t)s, kTagPass2, seed);
+            u[d] = (unsigned long long)x.x * th + (((unsigned long long)x.x * tl) >> 32);
+            wrow[d] = x.y;
+            home[d] = -1;
+        }
+        int lo[kP2Draws];
+#pragma unroll
+        for (int d = 0; d < kP2Draws; ++d) {  // first c with cdf[c] > u, from its guide bucket
+            const int k = (int)(u[d] * kGuide / total);
+            int a = guide[k], b = guide[k + 1];
+            while (a < b) {
+                const int m = (a + b) >> 1;
+                if (scdf[m] > u[d]) b = m;
+                else a = m + 1;
             }
-            c = lo;
-            r = (int)uniform_index(x.y, (uint32_t)ms);
-            const bool seen = (bm[(int64_t)r * W + (c >> 5)] >> (c & 31)) & 1u;
-            if (!seen) {
-                key = (uint32_t)r * (uint32_t)ns + (uint32_t)c;
-                uint32_t h = hash32(key) & (kHashSize - 1);
-                for (int probe = 0; probe < kHashSize; ++probe) {
-                    const uint32_t prev = atomicCAS(&hkey[h], kEmpty, key);
-                    if (prev == kEmpty || prev == key) {
-                        atomicMin(&htid[h], (int)threadIdx.x);
-                        hslot = (int)h;
-                        break;
-                    }
-                    h = (h + 1) & (kHashSize - 1);
+            lo[d] = a;
+        }
+        uint32_t word[kP2Draws];
+#pragma unroll
+        for (int d = 0; d < kP2Draws; ++d) {
+            const int c = lo[d], r = (int)uniform_index(wrow[d], (uint32_t)ms);
+            rc[d] = ((uint32_t)r << 16) | (uint32_t)c;
+            // L2 reads: other CTAs of the cluster set bits in earlier rounds (L1 is not coherent)
+            word[d] = tt[d] < cap_draws ? __ldcg(bm + (int64_t)r * W + (c >> 5)) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int d = 0; d < kP2Draws; ++d) {
+            const int r = (int)(rc[d] >> 16), c = (int)(rc[d] & 0xffffu);
+            if ((word[d] >> (c & 31)) & 1u) continue;  // observed (or past the draw cap)
+            const uint32_t key = (uint32_t)r * (uint32_t)ns + (uint32_t)c;
+            const uint32_t h = hash32(key);
+            const int k = (int)(h & (kP2Cluster - 1));
+            uint32_t* rk = cl.map_shared_rank(hkey, k);
+            int32_t* rt = cl.map_shared_rank(htid, k);
+            uint32_t p = (h >> 3) & (uint32_t)(hpart - 1);
+            tr[d] = (int)(tt[d] - t0);
+            for (int probe = 0; probe < hpart; ++probe) {
+                const uint32_t prev = atomicCAS(&rk[p], kEmpty, key);
+                if (prev == kEmpty || prev == key) {
+                    atomicMin(&rt[p], tr[d]);
+                    home[d] = k;
+                    slot[d] = (int)p;
+                    break;
                 }
-                cand = hslot >= 0;
+                p = (p + 1) & (uint32_t)(hpart - 1);
             }
+            if (home[d] < 0) latch(status, LT_ELIMIT);  // a full table part: not expected at load 1/2
         }
-        __syncthreads();
-        const bool first = cand && htid[hslot] == (int)threadIdx.x;
+        cl.sync();
+        int mine = 0;
+        uint32_t firstmask = 0;
+#pragma unroll
+        for (int d = 0; d < kP2Draws; ++d)
+            if (home[d] >= 0 && cl.map_shared_rank(htid, home[d])[slot[d]] == tr[d]) {
+                firstmask |= 1u << d;
+                ++mine;
+            }
         int tot;
-        const int rank = block_exclusive_scan<int>(first ? 1 : 0, ws, &tot);
-        if (first && accepted + rank < need) {
-            keyout[accepted + rank] = ((uint32_t)r << 16) | (uint32_t)c;
-            atomicOr(bm + (int64_t)r * W + (c >> 5), 1u << (c & 31));
+        int pos = block_exclusive_scan<int>(mine, ws, &tot);
+        if (threadIdx.x == 0) s_cnt = tot;
+        cl.sync();
+        int before = 0, round_total = 0;
+        for (int k = 0; k < kP2Cluster; ++k) {
+            const int ck = *cl.map_shared_rank(&s_cnt, k);
+            if (k < rank) before += ck;
+            round_total += ck;
         }
-        accepted += min((int64_t)tot, need - accepted);
-        for (int i = threadIdx.x; i < kHashSize; i += blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < kP2Draws; ++d)
+            if (firstmask & (1u << d)) {
+                const int64_t g = accepted + before + pos;
+                if (g < need) {
+                    keyout[g] = rc[d];
+                    const int r = (int)(rc[d] >> 16), c = (int)(rc[d] & 0xffffu);
+                    atomicOr(bm + (int64_t)r * W + (c >> 5), 1u << (c & 31));
+                }
+                ++pos;
+            }
+        accepted += min((int64_t)round_total, need - accepted);
+        for (int i = threadIdx.x; i < hpart; i += blockDim.x) {
             hkey[i] = kEmpty;
             htid[i] = 0x7fffffff;
         }
-        __syncthreads();
+        __threadfence();  // this round's bitmap bits before the next round's reads
+        cl.sync();
     }
-    if (threadIdx.x == 0) smp.cnt[s] = n1 + (int)accepted;
+    if (rank == 0 && threadIdx.x == 0) smp.cnt[s] = n1 + (int)accepted;
 }
 
 // ------------------------------------------------------------------ entry evaluation
@@ -1005,11 +1118,19 @@ extern "C" lt_status lt_sample_pass2(lt_ctx* ctx, const lt_frame* f, const float
     lt_status st;
     uint32_t* bm = (uint32_t*)lt_scratch(ctx, SCR_BITMAP, (size_t)S * stride * 4, &st);
     if (!bm) return st;
-    const size_t shm = (size_t)C * 8;
-    if (shm > 16 * 1024)
-        LT_CUDA(ctx, cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_pass2<<<S, kP2Threads, shm, ctx->stream>>>(*f, weights, rate, seed_ref(ctx, seed), *smp, bm, stride,
-                                                 ctx->d_status);
+    unsigned long long* cdf_all = (unsigned long long*)lt_scratch(ctx, SCR_P2_CDF, ((size_t)S * C + S + 64) * 8, &st);
+    if (!cdf_all) return st;
+    unsigned long long* total_all = cdf_all + (size_t)S * C;
+    k_p2_prep<<<S, 1024, 0, ctx->stream>>>(*f, weights, *smp, cdf_all, total_all, bm, stride);
+    LT_LAUNCH_CHECK(ctx, "k_p2_prep");
+    // each CTA's part of the round's hash table: 2 slots per draw of the CTA
+    const int hpart = 2 * kP2Block * kP2Draws;
+    const size_t shm = (size_t)C * 8 + (size_t)hpart * 8 + (size_t)(kGuide + 2) * 4;
+    if (shm > (size_t)220 * 1024)
+        return lt_fail(ctx, LT_EINVAL, "lt_sample_pass2: global cut too large for the pass-2 CDF in shared memory");
+    LT_CUDA(ctx, cudaFuncSetAttribute(k_pass2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    k_pass2<<<S * kP2Cluster, kP2Block, shm, ctx->stream>>>(*f, rate, seed_ref(ctx, seed), *smp, cdf_all, total_all, bm,
+                                                            stride, hpart, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_pass2");
     return LT_OK;
 }
