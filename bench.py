@@ -246,8 +246,10 @@ def run_ours(args):
         if ev:
             ev[5].record()
 
-    from paper_2202_12567_gb300 import proposal
+    from paper_2202_12567_gb300 import autotune, proposal
     theta = proposal.load_theta(device=local) if os.path.exists(proposal.DEFAULT_THETA) else None
+    # launch shapes for this workload: the shipped tuning cache, else tuned now
+    tune_key, tune_values, tune_cached = autotune.apply(R, args.workload)
 
     for i in range(args.warmup):
         frame(i)
@@ -391,6 +393,7 @@ def run_ours(args):
                             rel_rmse_paper_pdf=round(rel_g, 5),
                             plain_form_ms=round(plain_ms, 4), speedup_vs_plain_form=round(plain_ms / ms_frame, 3),
                             plain_equals_graph_bitwise=same_as_graph,
+                            tuning=dict(key=tune_key, values=tune_values, from_cache=tune_cached),
                             eval_roofline=roof_eval,
                             setup_ms=round(setup_ms, 1),
                             stage_ms=dict(zip(["pass1", "pass2", "eval", "complete", "render"],

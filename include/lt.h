@@ -219,6 +219,20 @@ lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int
 lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
                     const float* w, const int32_t* row_perm, float* img);
 
+/* ---- Launch tuning (no counterpart in the paper) ---------------------------
+ * Launch shapes the library lets a caller tune per workload; they change no result
+ * beyond the float summation order of the ALS Gram (als_lane_entries).  The values
+ * apply to later calls and to later graph captures of the context. */
+typedef struct {
+    int32_t eval_ctas_per_sm;   /* entry evaluation: persistent CTAs of 128 threads per SM (1..64), 16 */
+    int32_t ray_ctas_per_sm;    /* pass-1 shadow-ray kernels: the same (1..64), 16 */
+    int32_t als_lane_entries;   /* ALS (r <= 16): a line gets 2^g lanes so that a lane holds at most about
+                                   this many of its entries (16..1024), 96 */
+} lt_tuning;
+lt_status lt_get_tuning(const lt_ctx* ctx, lt_tuning* t);
+/* LT_EINVAL (and no change) if a value is out of range. */
+lt_status lt_set_tuning(lt_ctx* ctx, const lt_tuning* t);
+
 /* ---- Learned pass-2 proposal ---------------------------------------------
  * The paper draws pass-2 columns from the pass-1 estimate g (Sec. 5) and leaves a
  * learned importance to future work; these calls are that extension.  Rows of the

@@ -57,17 +57,18 @@ struct Omega {
     float* sval_c;
     int64_t sell_cap;
     int tcap;
+    int lane_entries;   // class threshold (line_class)
     bool sell;          // fill the sliced layout
     bool csr;           // fill CSR / CSC (the warp-group ALS for r > 16)
 };
 
 // Group-size classes of a line: class g gives a line of L entries G = 2^g lanes, so
-// that a lane takes at most about kLaneEntries of them (g = 0..5).
-constexpr int kLaneEntries = 96, kClasses = 6;
+// that a lane takes at most about `lane_entries` of them (g = 0..5; a tuning value).
+constexpr int kClasses = 6;
 
-__host__ __device__ inline int line_class(int len) {
+__host__ __device__ inline int line_class(int len, int lane_entries) {
     int g = 0;
-    while (g < kClasses - 1 && len > (kLaneEntries << g)) ++g;
+    while (g < kClasses - 1 && len > (lane_entries << g)) ++g;
     return g;
 }
 
@@ -182,12 +183,12 @@ constexpr int kOrdMax = 4096;
 // for class g) and cls[8..15): the first warp task of each, a class-g task covering
 // 32 / 2^g lines; cls[6] and cls[14] are the totals.
 __device__ void om_classes(const int32_t* __restrict__ cnt1, int n, const int32_t* __restrict__ ord, bool sorted,
-                           int32_t* __restrict__ cls) {
+                           int lane_entries, int32_t* __restrict__ cls) {
     __shared__ int32_t num[kClasses];
     if (threadIdx.x < kClasses) num[threadIdx.x] = 0;
     __syncthreads();
     if (sorted)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&num[line_class(cnt1[ord[i]])], 1);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&num[line_class(cnt1[ord[i]], lane_entries)], 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         if (!sorted) num[0] = n;  // unsorted: every line on one lane
@@ -287,9 +288,9 @@ __global__ void k_om_scan(lt_frame F, lt_samples smp, Omega om, const float* __r
     int32_t* rcls = om.rcls + (int64_t)s * 16;
     int32_t* ccls = om.ccls + (int64_t)s * 16;
     om_order(rc1, ms, rord, key);
-    om_classes(rc1, ms, rord, ms <= kOrdMax, rcls);
+    om_classes(rc1, ms, rord, ms <= kOrdMax, om.lane_entries, rcls);
     om_order(cc1, ns, cord, key);
-    om_classes(cc1, ns, cord, ns <= kOrdMax, ccls);
+    om_classes(cc1, ns, cord, ns <= kOrdMax, om.lane_entries, ccls);
     if (om.sell) {
         om_tasks(rc1, ms, rord, rcls, om.rpos + row0, om.rtb + (int64_t)s * om.tcap, om.rbase + s + 1, ws);
         om_tasks(cc1, ns, cord, ccls, om.cpos + (int64_t)s * F.C, om.ctb + (int64_t)s * om.tcap, om.cbase + s + 1,
@@ -1142,14 +1143,17 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.bt_stride = (int64_t)C * ((mr + 31) / 32);
     om.sell = r <= 16;
     om.csr = !om.sell;
-    // Sliced layout capacity.  Per slice and side, for lines sorted by count, the
-    // padding of a task is at most the entries of the task before it, rounding to a
-    // multiple of 4 slots adds at most 128 slots per task, and there are at most
-    // n / 32 + E_s / (48 * 32) + 6 tasks: at most E_s (1 + 1/48 + 1/12) + 5 n + L_max
-    // + 5 * 32 * kLaneEntries + 768 slots.  Beyond the capacity the scatter latches
-    // LT_ELIMIT.
+    // Sliced layout capacity, le = lane_entries.  Per slice and side, for lines sorted
+    // by count, the padding of a task is at most the entries of the task before it
+    // (the first task of class g < 5 adds at most 32 le slots, of class 5 at most
+    // L_max), rounding to a multiple of 4 adds at most 128 slots per task, and there
+    // are at most n / 32 + 2 E_s / (32 le) + 6 tasks (a class g > 0 line has more than
+    // le 2^(g-1) entries): at most E_s (1 + 8 / le) + 4 n + L_max + 160 le + 768 slots.
+    // Beyond the capacity the scatter latches LT_ELIMIT.
     const int64_t nmax = std::max<int64_t>(mr, C);
-    om.sell_cap = om.sell ? E + E / 32 + E / 16 + (int64_t)S * (5 * nmax + 5 * 32 * kLaneEntries + 1024) : 0;
+    om.lane_entries = ctx->tune.als_lane_entries;
+    const int64_t le = om.lane_entries;
+    om.sell_cap = om.sell ? E + (8 * E + le - 1) / le + E / 32 + (int64_t)S * (5 * nmax + 160 * le + 1024) : 0;
     om.tcap = (int)nmax + 8;
     const size_t e_csr = om.csr ? (size_t)E : 0, e_sell = (size_t)om.sell_cap;
     const size_t t_sell = om.sell ? (size_t)S * om.tcap : 0;

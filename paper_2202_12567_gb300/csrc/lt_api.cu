@@ -108,6 +108,21 @@ extern "C" lt_status lt_destroy(lt_ctx* ctx) {
 
 extern "C" int32_t* lt_status_word(lt_ctx* ctx) { return ctx ? ctx->d_status : nullptr; }
 
+extern "C" lt_status lt_get_tuning(const lt_ctx* ctx, lt_tuning* t) {
+    if (!ctx || !t) return LT_EINVAL;
+    *t = ctx->tune;
+    return LT_OK;
+}
+
+extern "C" lt_status lt_set_tuning(lt_ctx* ctx, const lt_tuning* t) {
+    if (!ctx || !t) return LT_EINVAL;
+    if (t->eval_ctas_per_sm < 1 || t->eval_ctas_per_sm > 64 || t->ray_ctas_per_sm < 1 || t->ray_ctas_per_sm > 64 ||
+        t->als_lane_entries < 16 || t->als_lane_entries > 1024)
+        return lt_fail(ctx, LT_EINVAL, "lt_set_tuning: value out of range");
+    ctx->tune = *t;
+    return LT_OK;
+}
+
 extern "C" int64_t lt_launch_count(const lt_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
 extern "C" lt_status lt_debug_scratch(lt_ctx* ctx, int32_t slot, void** ptr, int64_t* bytes) {

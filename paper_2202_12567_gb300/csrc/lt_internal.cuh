@@ -396,6 +396,7 @@ struct lt_ctx {
     const uint64_t* seed_dev = nullptr;    // device seed word of the graph being captured
     std::vector<void*> retired;            // scratch that live graphs may still reference
     int graphs = 0;                        // graphs alive on this context
+    lt_tuning tune{16, 16, 96};            // launch tuning (lt_set_tuning)
 };
 
 inline ltk::SeedRef seed_ref(const lt_ctx* ctx, uint64_t seed) { return ltk::SeedRef{seed, ctx->seed_dev}; }

@@ -1068,7 +1068,8 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     LT_LAUNCH_CHECK(ctx, "k_p1_draws");
     k_p1_kpfx<<<1, 1024, 0, ctx->stream>>>(*f, pl, w.kpfx);
     LT_LAUNCH_CHECK(ctx, "k_p1_kpfx");
-    k_p1_initial<<<16 * nsm, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, pl, store, w.kpfx);
+    const int ray_grid = ctx->tune.ray_ctas_per_sm * nsm;
+    k_p1_initial<<<ray_grid, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, pl, store, w.kpfx);
     LT_LAUNCH_CHECK(ctx, "k_p1_initial");
     k_p1_leafmean<<<grid_for((int64_t)S * C, 256), 256, 0, ctx->stream>>>(*f, pl, store, w.leafmean);
     LT_LAUNCH_CHECK(ctx, "k_p1_leafmean");
@@ -1093,7 +1094,7 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
         LT_LAUNCH_CHECK(ctx, "k_p1_setup");
         k_p1_setup_big<<<4 * nsm, 256, 0, ctx->stream>>>(*f, pl, store, w, h, ctx->d_status);
         LT_LAUNCH_CHECK(ctx, "k_p1_setup_big");
-        k_p1_rays<<<16 * nsm, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, store, w, h);
+        k_p1_rays<<<ray_grid, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, store, w, h);
         LT_LAUNCH_CHECK(ctx, "k_p1_rays");
         k_p1_decide<<<grid_for(npairs, 128), 128, 0, ctx->stream>>>(*f, pl, store, w, h);
         LT_LAUNCH_CHECK(ctx, "k_p1_decide");
@@ -1148,7 +1149,7 @@ extern "C" lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min
     if (shm > 16 * 1024)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
-    k_eval_entries<false><<<ctx->num_sms * 16, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
+    k_eval_entries<false><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
                                                                         nullptr);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries");
     return LT_OK;
@@ -1206,7 +1207,7 @@ extern "C" lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, flo
     if (shm > 16 * 1024)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
-    k_eval_entries<false><<<ctx->num_sms * 16, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
+    k_eval_entries<false><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
                                                                         nullptr);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries");
     return LT_OK;
@@ -1231,7 +1232,7 @@ extern "C" lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, 
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
     lt_samples copy = *smp;
-    k_eval_entries<true><<<ctx->num_sms * 16, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, copy, pfx,
+    k_eval_entries<true><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, copy, pfx,
                                                                        stats);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries<count>");
     unsigned long long h[4];

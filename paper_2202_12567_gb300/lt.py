@@ -63,6 +63,10 @@ class lt_params(ctypes.Structure):
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 32, 64, 10497
 
 
+class lt_tuning(ctypes.Structure):
+    _fields_ = [("eval_ctas_per_sm", _i32), ("ray_ctas_per_sm", _i32), ("als_lane_entries", _i32)]
+
+
 _SIGS = {
     "lt_status_str": (ctypes.c_char_p, [_i32]),
     "lt_last_error": (ctypes.c_char_p, [_p]),
@@ -97,6 +101,8 @@ _SIGS = {
                                       ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p, _p,
                                       ctypes.POINTER(_p)]),
     "lt_frame_graph_launch": (_i32, [_p, _u64]),
+    "lt_get_tuning": (_i32, [_p, ctypes.POINTER(lt_tuning)]),
+    "lt_set_tuning": (_i32, [_p, ctypes.POINTER(lt_tuning)]),
     "lt_proposal_features": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _p, _p]),
     "lt_proposal_forward": (_i32, [_p, _p, _p, _i64, _p, _p]),
     "lt_proposal_weights": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _p, _p, _f32, _p]),
@@ -524,3 +530,21 @@ def lt_proposal_grad(ctx: Context, theta, feat, target, group_off, ngroups, n, g
 def lt_proposal_adam(ctx: Context, theta, m, v, grad, step, lr):
     ctx._check("lt_proposal_adam", ctx.lib.lt_proposal_adam(ctx.h, _ptr(theta), _ptr(m), _ptr(v), _ptr(grad),
                                                             int(step), lr))
+
+
+# ------------------------------------------------------------------ launch tuning
+def lt_get_tuning(ctx: Context) -> dict:
+    t = lt_tuning()
+    ctx._check("lt_get_tuning", ctx.lib.lt_get_tuning(ctx.h, ctypes.byref(t)))
+    return {name: int(getattr(t, name)) for name, _ in lt_tuning._fields_}
+
+
+def lt_set_tuning(ctx: Context, **values):
+    """Set some tuning values (names of lt_tuning); the others keep their current value."""
+    cur = lt_get_tuning(ctx)
+    unknown = set(values) - set(cur)
+    if unknown:
+        raise KeyError(f"unknown tuning values: {sorted(unknown)}")
+    cur.update({k: int(v) for k, v in values.items()})
+    t = lt_tuning(*[cur[name] for name, _ in lt_tuning._fields_])
+    ctx._check("lt_set_tuning", ctx.lib.lt_set_tuning(ctx.h, ctypes.byref(t)))
