@@ -101,9 +101,11 @@ typedef struct {
 
 /* Completed factors: M_s ~= U_s V_s^T at rank r (the paper's X = U, Y = V^T). */
 typedef struct {
-    int32_t r;            /* rank, 1..32 */
+    int32_t r;            /* rank, 1..32; the row stride of U and V */
     float* U;             /* [m][r] rows in slice order */
     float* V;             /* [S][C][r] */
+    int32_t* rank;        /* [S] per-slice rank r_s <= r (values clamped to 1..r), or NULL: r
+                             for every slice; components r_s .. r-1 of a slice's rows are 0 */
 } lt_factors;
 
 const char* lt_status_str(lt_status s);
@@ -209,11 +211,15 @@ lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, float d_min, l
  * the box slab tests made.  Synchronous. */
 lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, const lt_samples* smp,
                         int64_t* stats_host);
-/* Masked ALS at rank r, `iters` sweeps (U-step then V-step), ridge lam_rel
- * trace(G)/r, V0 from Philox (k, j, slice, 3); float32 Cholesky with a float64
- * retry when min/max pivot^2 < 1e-6. */
+/* Masked ALS at rank r (uv->rank[s] per slice when given), `iters` sweeps (U-step
+ * then V-step), ridge lam_rel trace(G)/r, V0 from Philox (k, j, slice, 3); float32
+ * Cholesky with a float64 retry when min/max pivot^2 < 1e-6. */
 lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
                       float lam_rel, uint64_t seed, lt_factors* uv);
+/* Per-slice rank rule: rank[s] = min(R, max(8, 8 ceil(n'_s / cols))), a multiple of 8
+ * that grows with the slice's coarsened cut (n'_s after lt_sample_pass1). */
+lt_status lt_slice_ranks(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t R, int32_t cols,
+                         int32_t* rank);
 /* img[row_perm[slice_off[s] + i]] = max(0, u_i . (V_s^T w_s)); w NULL = all ones
  * (the column sum, Sec. 3 step 5), else w[S][C]. */
 lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
@@ -300,6 +306,8 @@ typedef struct {
     const float* proposal;/* theta of the learned proposal; when given (and weights is NULL)
                              pass 2 draws from its weights with mixing factor `mix` */
     float mix;
+    int32_t rank_cols;    /* > 0: after pass 1 the frame sets uv->rank by lt_slice_ranks with
+                             R = uv->r and cols = rank_cols (uv->rank must be given); 0: fixed */
 } lt_params;
 
 /* One frame as a sequence of launches on the context's stream: lt_sample_pass1,

@@ -70,9 +70,19 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
         v2 = np.zeros(0)
     res = SliceResult(p1=p1, p2_rows=r2, p2_cols=c2, p2_vals=v2, U=None, V=None, hit_cap=hit_cap)
     rows, cols, vals = res.omega()
-    res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, cfg["rank"], cfg["als_iters"],
+    res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["als_iters"],
                                       cfg["lam_rel"], seed, s)
     return res
+
+
+def slice_rank(cfg, n_s: int) -> int:
+    """The rank of a slice: cfg["rank"], or with cfg["rank_cols"] > 0 the per-slice
+    rule min(rank, max(8, 8 ceil(n' / rank_cols))) (a multiple of 8 growing with the
+    coarsened cut; our reading of the configuration's "rank 8-32 chosen per slice")."""
+    cols = int(cfg.get("rank_cols", 0))
+    if cols <= 0:
+        return int(cfg["rank"])
+    return int(min(cfg["rank"], max(8, 8 * -(-int(n_s) // cols))))
 
 
 def render_frame(scene, cfg, st=None, seed=None, slices=None):

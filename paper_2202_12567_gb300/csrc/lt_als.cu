@@ -62,6 +62,11 @@ struct Omega {
     bool csr;           // fill CSR / CSC (the warp-group ALS for r > 16)
 };
 
+// rank of slice s: rk[s] clamped to [1, R], or R when there are no per-slice ranks
+__device__ __forceinline__ int slice_rank(const int32_t* __restrict__ rk, int s, int R) {
+    return rk ? min(max(rk[s], 1), R) : R;
+}
+
 // Group-size classes of a line: class g gives a line of L entries G = 2^g lanes, so
 // that a lane takes at most about `lane_entries` of them (g = 0..5; a tuning value).
 constexpr int kClasses = 6;
@@ -398,15 +403,21 @@ __global__ void k_line_prefix(const lt_samples smp, int S, int64_t* pfx) {
     if (threadIdx.x == 0) pfx[S] = carry;
 }
 
-__global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int r, SeedRef sr, float* __restrict__ V) {
+__global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int R, const int32_t* __restrict__ rk, SeedRef sr,
+                           float* __restrict__ V) {
     const int s = blockIdx.y;
     const uint64_t seed = sr.get();
     const int ns = smp.ncol[s];
+    const int r = slice_rank(rk, s, R);  // the slice's rank; components r .. R-1 are 0
     const float amp = sqrtf(fmaxf(om.mu[s], 0.f) / (float)r);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns * r; i += gridDim.x * blockDim.x) {
-        const int j = i / r, k = i % r;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns * R; i += gridDim.x * blockDim.x) {
+        const int j = i / R, k = i % R;
+        if (k >= r) {
+            V[((int64_t)s * F.C + j) * R + k] = 0.f;
+            continue;
+        }
         const uint32_t w = philox((uint32_t)k, (uint32_t)j, (uint32_t)s, kTagAlsInit, seed).x;
-        V[((int64_t)s * F.C + j) * r + k] = amp * (0.5f + (float)w * 2.3283064365386963e-10f);
+        V[((int64_t)s * F.C + j) * R + k] = amp * (0.5f + (float)w * 2.3283064365386963e-10f);
     }
 }
 
@@ -636,7 +647,8 @@ template <int RP>
 __host__ __device__ constexpr int als_warps() { return RP == 32 ? 8 : 16; }
 
 template <int RP>
-__global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F, lt_samples smp, Omega om, int r,
+__global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F, lt_samples smp, Omega om, int R,
+                                                                   const int32_t* __restrict__ rk,
                                                                    float lam_rel, bool rows_side,
                                                                    const float* __restrict__ Fin,
                                                                    float* __restrict__ Fout, int32_t* n_fp64,
@@ -649,23 +661,25 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
     const int s = blockIdx.y, P = gridDim.x, p = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int grp = lane / RP, k = lane % RP;
+    const int r = slice_rank(rk, s, R);  // the slice's rank (factor rows have stride R)
+    if (rk && r <= 16) return;           // per-slice ranks: the lane-group kernel has these slices
     const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
     const int ns = smp.ncol[s];
     const int nlines = rows_side ? ms : ns;
     const int l0 = (int)((int64_t)nlines * p / P), l1 = (int)((int64_t)nlines * (p + 1) / P);
     if (l0 >= l1) return;
-    const float* src = rows_side ? Fin + (int64_t)s * F.C * r : Fin + (int64_t)row0 * r;
+    const float* src = rows_side ? Fin + (int64_t)s * F.C * R : Fin + (int64_t)row0 * R;
     const int nsrc = rows_side ? ns : ms;
     const bool staged = nsrc <= stage_rows;
     if (staged) {
         for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
             const int row = i / RP, c = i % RP;
-            stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * r + c) : 0.f;
+            stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * R + c) : 0.f;
         }
     }
     __syncthreads();
     const float* Fb = staged ? stage : src;
-    const int fstride = staged ? RP + 1 : r;
+    const int fstride = staged ? RP + 1 : R;
     const int64_t o = smp.off[s];
     for (int base = l0 + wid * LPW; base < l1; base += NW * LPW) {
         int my_len = 0;
@@ -684,14 +698,14 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
                 len = rp[line + 1] - b;
                 idx = om.cidx + o + b;
                 vv = om.cval + o + b;
-                dst = Fout + (int64_t)(row0 + line) * r;           // U row
+                dst = Fout + (int64_t)(row0 + line) * R;           // U row
             } else {
                 const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
                 const int b = cp[line];
                 len = cp[line + 1] - b;
                 idx = om.ridx + o + b;
                 vv = om.rval + o + b;
-                dst = Fout + ((int64_t)s * F.C + line) * r;        // V row
+                dst = Fout + ((int64_t)s * F.C + line) * R;        // V row
             }
             gram_tc<RP>(len, idx, vv, Fb, fstride, r, &Gs_all[wid][q][0], &bs_all[wid][q][0]);
             if (grp == q) {
@@ -715,7 +729,7 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
                 if (k == 0) atomicAdd(n_fp64, 1);
             }
         }
-        if (live && k < r) my_dst[k] = xf;
+        if (live && k < R) my_dst[k] = k < r ? xf : 0.f;
         __syncwarp();
     }
 }
@@ -738,6 +752,7 @@ struct AlsQueue {
     float* gram;        // [cap][kVals] Gram lower triangle then right-hand side
     int64_t cap;
     int32_t* status;    // device status word (LT_ELIMIT when the queue overflows)
+    int32_t* rank;      // [cap] rank of each queued line
 };
 
 // Cholesky solve of (G + lam I) u = b in place (u returned in b); rows i >= r are
@@ -818,8 +833,8 @@ __device__ __forceinline__ int stage_slot(int j, int q) {
 // stream (chunks of 4 at idx4[32 c], vv4[32 c]) to a and bb, in stream order.
 template <int RP>
 __device__ __forceinline__ void stream_gram(int nk, const uint2* __restrict__ idx4, const float4* __restrict__ vv4,
-                                            int r, const float* __restrict__ src, bool staged, const float4* stage4,
-                                            float (&a)[RP * (RP + 1) / 2], float (&bb)[RP]) {
+                                            int r, int R, const float* __restrict__ src, bool staged,
+                                            const float4* stage4, float (&a)[RP * (RP + 1) / 2], float (&bb)[RP]) {
     constexpr int NQ = RP / 4;
     const int nc = (nk + 3) >> 2;
     // the next two chunks' loads are in flight during this chunk's four entries
@@ -850,7 +865,7 @@ __device__ __forceinline__ void stream_gram(int nk, const uint2* __restrict__ id
                     }
                 } else {
 #pragma unroll
-                    for (int cc = 0; cc < RP; ++cc) x[cc] = cc < r ? __ldg(src + (int64_t)j * r + cc) : 0.f;
+                    for (int cc = 0; cc < RP; ++cc) x[cc] = cc < r ? __ldg(src + (int64_t)j * R + cc) : 0.f;
                 }
 #pragma unroll
                 for (int i = 0; i < RP; ++i) {
@@ -871,7 +886,7 @@ __device__ __forceinline__ void stream_gram(int nk, const uint2* __restrict__ id
 // One lane of a warp task: `line` (or -1) is its line, `sub` its rank among the G
 // lanes of the line, `slot` the first slot of its stream (task base + 4 lane).
 template <int RP>
-__device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int r, bool rows_side,
+__device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int r, int R, bool rows_side,
                                          const float* __restrict__ src, bool staged, const float4* stage4,
                                          float* __restrict__ Fout, float lam_rel, const AlsQueue<RP>& q, int s,
                                          int line, int sub, int G, int64_t slot) {
@@ -896,7 +911,7 @@ __device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int
     for (int i = 0; i < RP; ++i) bb[i] = 0.f;
     const int nk = sub < len ? (len - sub + G - 1) / G : 0;
     stream_gram<RP>(nk, reinterpret_cast<const uint2*>(sidx + slot), reinterpret_cast<const float4*>(sval + slot), r,
-                    src, staged, stage4, a, bb);
+                    R, src, staged, stage4, a, bb);
     if (G > 1) {  // the group's partial sums into its first lane (G is warp-uniform)
         for (int m = G >> 1; m > 0; m >>= 1) {
 #pragma unroll
@@ -906,7 +921,8 @@ __device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int
         }
     }
     if (line < 0 || sub != 0) return;
-    const int64_t dst = rows_side ? (int64_t)(row0 + line) * r : ((int64_t)s * F.C + line) * r;
+    const int64_t dst = rows_side ? (int64_t)(row0 + line) * R : ((int64_t)s * F.C + line) * R;
+    for (int i = r; i < R; ++i) Fout[dst + i] = 0.f;  // components beyond the slice's rank
     if (chol_solve<RP, float>(a, bb, r, lam_rel, true)) {
 #pragma unroll
         for (int i = 0; i < RP; ++i)
@@ -925,8 +941,9 @@ __device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int
     for (int i = 0; i < RP; ++i) bb[i] = 0.f;
     for (int u = 0; u < G; ++u)
         stream_gram<RP>(u < len ? (len - u + G - 1) / G : 0, reinterpret_cast<const uint2*>(sidx + slot + 4 * u),
-                        reinterpret_cast<const float4*>(sval + slot + 4 * u), r, src, staged, stage4, a, bb);
+                        reinterpret_cast<const float4*>(sval + slot + 4 * u), r, R, src, staged, stage4, a, bb);
     q.dst[qs] = dst;
+    q.rank[qs] = r;
     float* gq = q.gram + (int64_t)qs * AlsQueue<RP>::kVals;
 #pragma unroll
     for (int i = 0; i < NA; ++i) gq[i] = a[i];
@@ -934,11 +951,12 @@ __device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int
     for (int i = 0; i < RP; ++i) gq[NA + i] = bb[i];
 }
 
-// stage the slice's source factor rows (nsrc x r, zero-padded to RP) in shared memory
+// stage the slice's source factor rows (nsrc rows of stride R, the first r values,
+// zero-padded to RP) in shared memory
 template <int RP>
-__device__ __forceinline__ void stage_factors(const float* __restrict__ src, int nsrc, int r, float4* stage4) {
+__device__ __forceinline__ void stage_factors(const float* __restrict__ src, int nsrc, int r, int R, float4* stage4) {
     constexpr int NQ = RP / 4;
-    if (r == RP) {
+    if (r == RP && R == RP) {
         const float4* src4 = reinterpret_cast<const float4*>(src);
         for (int i = threadIdx.x; i < nsrc * NQ; i += blockDim.x)
             stage4[stage_slot<RP>(i / NQ, i % NQ)] = __ldg(src4 + i);
@@ -947,7 +965,7 @@ __device__ __forceinline__ void stage_factors(const float* __restrict__ src, int
             const int row = i / NQ, q4 = i % NQ;
             float v[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = 4 * q4 + c < r ? __ldg(src + (int64_t)row * r + 4 * q4 + c) : 0.f;
+            for (int c = 0; c < 4; ++c) v[c] = 4 * q4 + c < r ? __ldg(src + (int64_t)row * R + 4 * q4 + c) : 0.f;
             stage4[stage_slot<RP>(row, q4)] = make_float4(v[0], v[1], v[2], v[3]);
         }
     }
@@ -958,7 +976,8 @@ __device__ __forceinline__ void stage_factors(const float* __restrict__ src, int
 // of the side; for each slice it touches it stages the source factor rows once and
 // its warps take that slice's tasks from a shared counter.
 template <int RP>
-__global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp, Omega om, int r, bool rows_side,
+__global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp, Omega om, int R,
+                                                    const int32_t* __restrict__ rk, bool rows_side,
                                                     const float* __restrict__ Fin, float* __restrict__ Fout,
                                                     float lam_rel, AlsQueue<RP> q, int stage_rows) {
     extern __shared__ float4 stage4[];
@@ -1035,15 +1054,17 @@ __global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp,
         const int sl = s_slice;
         if (sl < 0) break;
         const int row0 = F.slice_off[sl], ms = F.slice_off[sl + 1] - row0, ns = smp.ncol[sl];
-        const float* src = rows_side ? Fin + (int64_t)sl * F.C * r : Fin + (int64_t)row0 * r;
+        const int r = slice_rank(rk, sl, R);  // the slice's rank (factor rows have stride R)
+        const bool mine = r <= RP;      // per-slice ranks above RP are the warp-group kernel's
+        const float* src = rows_side ? Fin + (int64_t)sl * F.C * R : Fin + (int64_t)row0 * R;
         const int nsrc = rows_side ? ns : ms;
         const bool staged = nsrc <= stage_rows;
-        if (staged) stage_factors<RP>(src, nsrc, r, stage4);
+        if (staged && mine) stage_factors<RP>(src, nsrc, r, R, stage4);
         __syncthreads();
         const int32_t* ord = rows_side ? om.rord + row0 : om.cord + (int64_t)sl * F.C;
         const int32_t* cls = (rows_side ? om.rcls : om.ccls) + (int64_t)sl * 16;
         const int32_t* tb = (rows_side ? om.rtb : om.ctb) + (int64_t)sl * om.tcap;
-        const int t1 = s_t1;
+        const int t1 = mine ? s_t1 : 0;
         for (;;) {
             int tk = 0;
             if (lane == 0) tk = atomicAdd(&s_next, 1);
@@ -1054,7 +1075,7 @@ __global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp,
             const int g = kClasses - 1 - k, G = 1 << g;
             const int li = cls[k] + (tk - cls[8 + k]) * (32 >> g) + (lane >> g);
             const bool live = li < cls[k + 1];
-            als_line<RP>(F, om, r, rows_side, src, staged, stage4, Fout, lam_rel, q, sl, live ? ord[li] : -1,
+            als_line<RP>(F, om, r, R, rows_side, src, staged, stage4, Fout, lam_rel, q, sl, live ? ord[li] : -1,
                          lane & (G - 1), G, base[sl] + tb[tk] + 4 * lane);
         }
         __syncthreads();  // the stage is reused by the next segment
@@ -1063,7 +1084,7 @@ __global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp,
 
 // float64 solve of the queued lines (grid-stride over the device count)
 template <int RP>
-__global__ void __launch_bounds__(64) k_als_retry(AlsQueue<RP> q, int r, float lam_rel, float* __restrict__ Fout,
+__global__ void __launch_bounds__(64) k_als_retry(AlsQueue<RP> q, float lam_rel, float* __restrict__ Fout,
                                                   int32_t* __restrict__ n_fp64) {
     constexpr int NA = RP * (RP + 1) / 2;
     const int n = min((int64_t)*q.count, q.cap);
@@ -1074,6 +1095,7 @@ __global__ void __launch_bounds__(64) k_als_retry(AlsQueue<RP> q, int r, float l
         for (int i = 0; i < NA; ++i) a[i] = gq[i];
 #pragma unroll
         for (int i = 0; i < RP; ++i) b[i] = gq[NA + i];
+        const int r = q.rank[t];
         chol_solve<RP, double>(a, b, r, lam_rel, false);
         float* d = Fout + q.dst[t];
 #pragma unroll
@@ -1113,6 +1135,14 @@ __global__ void k_render(lt_frame F, lt_samples smp, const float* __restrict__ U
     }
 }
 
+// r_s = min(R, max(8, 8 ceil(n'_s / cols))): a multiple of 8 growing with the coarsened cut
+__global__ void k_slice_ranks(lt_samples smp, int S, int R, int cols, int32_t* __restrict__ rank) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+        const int n = smp.ncol[s];
+        rank[s] = min(R, max(8, 8 * ((n + cols - 1) / cols)));
+    }
+}
+
 bool frame_ok2(const lt_frame* f) {
     return f && f->slice_off && f->S > 0 && f->S <= 1024 && f->m > 0 && f->C >= 1 && f->max_rows >= 0 &&
            f->max_rows <= 65535;
@@ -1137,12 +1167,15 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         ctx->plan.entries = E;
     }
     const int64_t mr = std::max(f->max_rows, 1);
-    const int r = uv->r;
+    const int R = uv->r;            // stride of the factor rows, the largest rank
+    const int32_t* rk = uv->rank;   // per-slice ranks (NULL: R for every slice)
     Omega om;
     om.bm_stride = mr * ((C + 31) / 32);
     om.bt_stride = (int64_t)C * ((mr + 31) / 32);
-    om.sell = r <= 16;
-    om.csr = !om.sell;
+    // the lane-group ALS takes slices of rank <= 16 (sliced layout), the warp-group
+    // ALS the others (CSR / CSC); with per-slice ranks above 16 both run
+    om.sell = R <= 16 || rk != nullptr;
+    om.csr = R > 16;
     // Sliced layout capacity, le = lane_entries.  Per slice and side, for lines sorted
     // by count, the padding of a task is at most the entries of the task before it
     // (the first task of class g < 5 adds at most 32 le slots, of class 5 at most
@@ -1198,7 +1231,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.sval_c = (float*)take(e_sell * 4);
     if ((size_t)(p - (char*)ctx->scr[SCR_OMEGA]) > ctx->scr_size[SCR_OMEGA])
         return lt_fail(ctx, LT_ENOMEM, "lt_complete: Omega layout overflow");
-    const int RP = r <= 8 ? 8 : r <= 16 ? 16 : 32;
+    const int RP = R <= 8 ? 8 : 16;  // lane-group kernel for ranks up to RP
     // per half-step retry counters, the float64 count, the mean partials
     constexpr int kOmParts = 8;
     const int nq = std::max(1, 2 * iters);
@@ -1225,68 +1258,75 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     LT_LAUNCH_CHECK(ctx, "k_om_scatter");
     k_line_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, S, om.line_pfx);
     LT_LAUNCH_CHECK(ctx, "k_line_prefix");
-    k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, r, seed_ref(ctx, seed), uv->V);
+    k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, R, rk, seed_ref(ctx, seed), uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
-    if (RP <= 16) {
-        // one thread per line; one 256-thread CTA per SM stages the slice's factor
-        // rows (up to 110 KB) in shared memory and leaves the rest of the SM's
-        // 256 KB to L1 for the lines' entry streams
-        const size_t row_bytes = (size_t)RP * 4;
-        const int stage_rows = (int)std::min<int64_t>((110 * 1024) / row_bytes, std::max<int64_t>(mr, C));
-        const size_t dyn = (size_t)stage_rows * row_bytes;
-        const int64_t cap = std::min<int64_t>(std::max<int64_t>(f->m, (int64_t)S * C), 1 << 18);
+    // lane-group kernel: one thread (group) per line; one 256-thread CTA per SM stages
+    // the slice's factor rows (up to 110 KB) and leaves the rest of the SM to L1
+    const size_t row_bytes = (size_t)RP * 4;
+    const int stage_rows = (int)std::min<int64_t>((110 * 1024) / row_bytes, std::max<int64_t>(mr, C));
+    const size_t dyn = (size_t)stage_rows * row_bytes;
+    const int64_t cap = std::min<int64_t>(std::max<int64_t>(f->m, (int64_t)S * C), 1 << 18);
+    int64_t* qdst = nullptr;
+    float* qgram = nullptr;
+    int32_t* qrank = nullptr;
+    if (om.sell) {
         const int kv = RP * (RP + 1) / 2 + RP;
-        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, (size_t)cap * (8 + (size_t)kv * 4) + 512, &st);
+        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, (size_t)cap * (12 + (size_t)kv * 4) + 1024, &st);
         if (!qp) return st;
-        int64_t* qdst = (int64_t*)qp;
-        float* qgram = (float*)(qp + (((size_t)cap * 8 + 255) & ~(size_t)255));
-        const unsigned gx = (unsigned)std::max<int64_t>(1, (mr + 255) / 256);
-        for (int it = 0; it < iters; ++it) {
-            for (int side = 0; side < 2; ++side) {
-                const bool rows = side == 0;
-                const float* fin = rows ? uv->V : uv->U;
-                float* fout = rows ? uv->U : uv->V;
-                int32_t* cnt = qcount + 2 * it + side;
-                if (RP == 8) {
-                    AlsQueue<8> q{cnt, qdst, qgram, cap, ctx->d_status};
-                    LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)dyn));
-                    k_als_line<8><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout, lam_rel,
-                                                                          q, stage_rows);
-                    LT_LAUNCH_CHECK(ctx, "k_als_line");
-                    k_als_retry<8><<<2 * nsm, 64, 0, ctx->stream>>>(q, r, lam_rel, fout, n64);
-                    LT_LAUNCH_CHECK(ctx, "k_als_retry");
-                } else {
-                    AlsQueue<16> q{cnt, qdst, qgram, cap, ctx->d_status};
-                    LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)dyn));
-                    k_als_line<16><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, r, rows, fin, fout,
-                                                                           lam_rel, q, stage_rows);
-                    LT_LAUNCH_CHECK(ctx, "k_als_line");
-                    k_als_retry<16><<<2 * nsm, 64, 0, ctx->stream>>>(q, r, lam_rel, fout, n64);
-                    LT_LAUNCH_CHECK(ctx, "k_als_retry");
-                }
-            }
-        }
-        return LT_OK;
+        qdst = (int64_t*)qp;
+        qrank = (int32_t*)(qp + (((size_t)cap * 8 + 255) & ~(size_t)255));
+        qgram = (float*)((char*)qrank + (((size_t)cap * 4 + 255) & ~(size_t)255));
+        if (RP == 8)
+            LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+        else
+            LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     }
-    // r > 16: one warp group per line on the tensor cores
+    // warp-group kernel: ranks above 16 on the tensor cores
     const int P = std::max(1, (2 * ctx->num_sms + S - 1) / S);
-    const size_t stat = (size_t)8 * (RP * (RP + 1) + RP) * 4;
-    const size_t budget = (size_t)210 * 1024 > stat ? (size_t)210 * 1024 - stat : 0;
-    const int stage_rows = (int)std::min<size_t>(budget / ((RP + 1) * 4), (size_t)1 << 20);
-    const size_t dyn = (size_t)stage_rows * (RP + 1) * 4;
-    LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    const size_t hstat = (size_t)8 * (32 * 33 + 32) * 4;
+    const size_t hbudget = (size_t)210 * 1024 > hstat ? (size_t)210 * 1024 - hstat : 0;
+    const int hstage_rows = (int)std::min<size_t>(hbudget / (33 * 4), (size_t)1 << 20);
+    const size_t hdyn = (size_t)hstage_rows * 33 * 4;
+    if (om.csr)
+        LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hdyn));
     for (int it = 0; it < iters; ++it) {
         for (int side = 0; side < 2; ++side) {
             const bool rows = side == 0;
             const float* fin = rows ? uv->V : uv->U;
             float* fout = rows ? uv->U : uv->V;
-            k_als_half<32><<<dim3(P, S), 32 * als_warps<32>(), dyn, ctx->stream>>>(*f, *smp, om, r, lam_rel, rows,
-                                                                                    fin, fout, n64, stage_rows);
-            LT_LAUNCH_CHECK(ctx, "k_als_half");
+            int32_t* cnt = qcount + 2 * it + side;
+            if (om.sell && RP == 8) {
+                AlsQueue<8> q{cnt, qdst, qgram, cap, ctx->d_status, qrank};
+                k_als_line<8><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, R, rk, rows, fin, fout, lam_rel, q,
+                                                              stage_rows);
+                LT_LAUNCH_CHECK(ctx, "k_als_line");
+                k_als_retry<8><<<2 * nsm, 64, 0, ctx->stream>>>(q, lam_rel, fout, n64);
+                LT_LAUNCH_CHECK(ctx, "k_als_retry");
+            } else if (om.sell) {
+                AlsQueue<16> q{cnt, qdst, qgram, cap, ctx->d_status, qrank};
+                k_als_line<16><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, R, rk, rows, fin, fout, lam_rel, q,
+                                                               stage_rows);
+                LT_LAUNCH_CHECK(ctx, "k_als_line");
+                k_als_retry<16><<<2 * nsm, 64, 0, ctx->stream>>>(q, lam_rel, fout, n64);
+                LT_LAUNCH_CHECK(ctx, "k_als_retry");
+            }
+            if (om.csr) {
+                k_als_half<32><<<dim3(P, S), 32 * als_warps<32>(), hdyn, ctx->stream>>>(
+                    *f, *smp, om, R, rk, lam_rel, rows, fin, fout, n64, hstage_rows);
+                LT_LAUNCH_CHECK(ctx, "k_als_half");
+            }
         }
     }
+    return LT_OK;
+}
+
+extern "C" lt_status lt_slice_ranks(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t R, int32_t cols,
+                                    int32_t* rank) {
+    if (!ctx || !frame_ok2(f) || !smp || !smp->ncol || !rank || R < 1 || R > 32 || cols < 1)
+        return lt_fail(ctx, LT_EINVAL, "lt_slice_ranks: bad arguments");
+    cudaSetDevice(ctx->device);
+    k_slice_ranks<<<(f->S + 255) / 256, 256, 0, ctx->stream>>>(*smp, f->S, R, cols, rank);
+    LT_LAUNCH_CHECK(ctx, "k_slice_ranks");
     return LT_OK;
 }
 

@@ -24,13 +24,17 @@ __global__ void k_set_seed(uint64_t* dst, uint64_t seed) { *dst = seed; }
 
 bool params_ok(const lt_params* p) {
     return p && p->rate1 >= 0.f && p->tau >= 0.f && p->d_min >= 0.f && p->rate >= 0.f && p->als_iters >= 0 &&
-           p->lam_rel >= 0.f && (!p->proposal || (p->mix >= 0.f && p->mix <= 1.f));
+           p->lam_rel >= 0.f && (!p->proposal || (p->mix >= 0.f && p->mix <= 1.f)) && p->rank_cols >= 0;
 }
 
 lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed, lt_samples* smp,
                     lt_factors* uv, const int32_t* row_perm, float* img) {
     lt_status st = lt_sample_pass1(ctx, f, p->rate1, p->tau, p->d_min, seed, smp);
     if (st != LT_OK) return st;
+    if (p->rank_cols > 0) {  // per-slice ranks from the coarsened cut
+        st = lt_slice_ranks(ctx, f, smp, uv->r, p->rank_cols, uv->rank);
+        if (st != LT_OK) return st;
+    }
     const float* w = p->weights;
     if (!w && p->proposal) {
         // learned proposal: features -> logits -> mixed weights, all on the stream
@@ -63,14 +67,14 @@ lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t
 
 extern "C" lt_status lt_render_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed,
                                      lt_samples* smp, lt_factors* uv, const int32_t* row_perm, float* img) {
-    if (!ctx || !f || !params_ok(p) || !smp || !uv || !row_perm || !img)
+    if (!ctx || !f || !params_ok(p) || !smp || !uv || !row_perm || !img || (p->rank_cols > 0 && !uv->rank))
         return lt_fail(ctx, LT_EINVAL, "lt_render_frame: bad arguments");
     return run_frame(ctx, f, p, seed, smp, uv, row_perm, img);
 }
 
 extern "C" lt_status lt_frame_graph_capture(lt_ctx* ctx, const lt_frame* f, const lt_params* p, lt_samples* smp,
                                             lt_factors* uv, const int32_t* row_perm, float* img, lt_graph** out) {
-    if (!ctx || !f || !params_ok(p) || !smp || !uv || !row_perm || !img || !out)
+    if (!ctx || !f || !params_ok(p) || !smp || !uv || !row_perm || !img || !out || (p->rank_cols > 0 && !uv->rank))
         return lt_fail(ctx, LT_EINVAL, "lt_frame_graph_capture: bad arguments");
     *out = nullptr;
     cudaSetDevice(ctx->device);

@@ -52,12 +52,12 @@ class lt_samples(ctypes.Structure):
 
 
 class lt_factors(ctypes.Structure):
-    _fields_ = [("r", _i32), ("U", _p), ("V", _p)]
+    _fields_ = [("r", _i32), ("U", _p), ("V", _p), ("rank", _p)]
 
 
 class lt_params(ctypes.Structure):
     _fields_ = [("rate1", _f32), ("tau", _f32), ("d_min", _f32), ("rate", _f32), ("als_iters", _i32),
-                ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32)]
+                ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32), ("rank_cols", _i32)]
 
 
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 32, 64, 10497
@@ -102,6 +102,7 @@ _SIGS = {
                                       ctypes.POINTER(_p)]),
     "lt_frame_graph_launch": (_i32, [_p, _u64]),
     "lt_get_tuning": (_i32, [_p, ctypes.POINTER(lt_tuning)]),
+    "lt_slice_ranks": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _i32, _p]),
     "lt_set_tuning": (_i32, [_p, ctypes.POINTER(lt_tuning)]),
     "lt_proposal_features": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _p, _p]),
     "lt_proposal_forward": (_i32, [_p, _p, _p, _i64, _p, _p]),
@@ -352,12 +353,15 @@ class Samples:
 
 
 class Factors:
-    def __init__(self, frame: Frame, r: int):
+    """U, V with row stride r; per_slice=True adds the per-slice rank array [S]."""
+
+    def __init__(self, frame: Frame, r: int, per_slice: bool = False):
         dev = frame.pts_s.device
         self.r = r
         self.U = torch.zeros(frame.m * r, dtype=torch.float32, device=dev)
         self.V = torch.zeros(frame.S * frame.C * r, dtype=torch.float32, device=dev)
-        self._s = lt_factors(r, _ptr(self.U), _ptr(self.V))
+        self.rank = torch.full((frame.S,), r, dtype=torch.int32, device=dev) if per_slice else None
+        self._s = lt_factors(r, _ptr(self.U), _ptr(self.V), _ptr(self.rank))
 
     def struct(self) -> lt_factors:
         return self._s
@@ -402,9 +406,18 @@ def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, i
 
 
 def params(cfg: dict, weights=None, proposal=None, mix: float = 0.8) -> lt_params:
-    """lt_params of a configuration dict (rate1, tau, d_min, rate, als_iters, lam_rel)."""
+    """lt_params of a configuration dict (rate1, tau, d_min, rate, als_iters, lam_rel,
+    rank_cols: 0 or absent = one rank per frame)."""
     return lt_params(cfg["rate1"], cfg["tau"], cfg["d_min"], cfg["rate"], cfg["als_iters"], cfg["lam_rel"],
-                     _ptr(weights), _ptr(proposal), mix)
+                     _ptr(weights), _ptr(proposal), mix, int(cfg.get("rank_cols", 0)))
+
+
+def lt_slice_ranks(ctx: Context, frame: Frame, smp: Samples, R: int, cols: int, rank=None):
+    if rank is None:
+        rank = torch.zeros(frame.S, dtype=torch.int32, device=frame.pts_s.device)
+    ctx._check("lt_slice_ranks", ctx.lib.lt_slice_ranks(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
+                                                        int(R), int(cols), _ptr(rank)))
+    return rank
 
 
 def lt_render_frame(ctx: Context, frame: Frame, prm: lt_params, seed, smp: Samples, uv: Factors, row_perm, img):

@@ -62,7 +62,7 @@ class Renderer:
         self.pts_s = lt.lt_permute_points(ctx, self.pts, row_perm)
         self.frame = lt.Frame(self.pts_s, self.vpls, slice_off, self.tree, cut, forest, level_off, level_nodes, H)
         self.smp = lt.Samples(self.frame, cfg["rate"], cfg["rate1"])
-        self.uv = lt.Factors(self.frame, cfg["rank"])
+        self.uv = lt.Factors(self.frame, cfg["rank"], per_slice=int(cfg.get("rank_cols", 0)) > 0)
         self.img = torch.zeros(self.frame.m, dtype=torch.float32, device=self.dev)
         lt.lt_sync(ctx)
         return self
@@ -80,6 +80,8 @@ class Renderer:
 
     def complete(self, seed):
         c = self.cfg
+        if int(c.get("rank_cols", 0)) > 0:  # per-slice ranks from the coarsened cut
+            lt.lt_slice_ranks(self.ctx, self.frame, self.smp, c["rank"], c["rank_cols"], self.uv.rank)
         lt.lt_complete(self.ctx, self.frame, self.smp, self.uv, c["als_iters"], c["lam_rel"], seed)
 
     def render_image(self, w=None):
