@@ -167,9 +167,9 @@ def eval_roofline(lt, ctx, R, stage_ms, clk):
 
 
 # DRAM bytes per ALS half-step launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of k_als_line<16>: U-step 40,988,160,
-# V-step 42,793,472; their mean)
-ALS_TRAFFIC_BYTES = 41_890_816
+# dram__bytes_write.sum of one ncu capture of k_als_line<16>: U-step 40,989,952,
+# V-step 42,801,408; their mean)
+ALS_TRAFFIC_BYTES = 41_895_680
 
 
 def als_roofline(lt, ctx, R, half_ms):
