@@ -351,7 +351,6 @@ __device__ __forceinline__ int lower_bound(const T* a, int n, T x) {
 enum ScratchSlot {
     SCR_P1_PLAN = 0,    // per slice per forest node: k, cap, off, cnt, cost, state
     SCR_P1_STORE,       // node storage (rows, v0, v1)
-    SCR_P1_SLICE,       // per slice totals and bases
     SCR_BITMAP,         // per slice observed-entry bitmaps (row-major and column-major)
     SCR_OMEGA,          // CSR / CSC of the observed entries
     SCR_ALS,            // per-slice statistics for ALS

@@ -1,14 +1,16 @@
 // Sampling passes of the sparse renderer.
 //
-//  * Pass 1 and light coarsening (Sec. 4, Eq. 2): one CTA per slice draws k_c rows
-//    for every global-cut node, evaluates them, then walks the cut's ancestor
-//    forest level by level.  A warp tests one sibling pair: it merges the two
-//    sorted row sets (zeta_f = zeta_a U zeta_b), evaluates the missing entries,
-//    reduces eps = max |V_q - V_p I_q / I_p| and merges when
-//    cost = eps + cost(q) < tau * S_hat.
-//  * Pass 2 (Sec. 5, Eq. 3): one CTA per slice draws (column from the integer CDF
-//    of g, row uniform) in blocks of blockDim draws, keeps the first occurrence of
-//    every new entry in draw order, and stops at ceil(rate m' n') entries.
+//  * Pass 1 and light coarsening (Sec. 4, Eq. 2): the cut nodes of every slice draw
+//    their k_c rows and evaluate them (one kernel over all slices), then the cut's
+//    ancestor forest is walked level by level with a few kernels per level over all
+//    slices: sibling pairs are laid out as the union zeta_f = zeta_a U zeta_b (one
+//    thread per small pair, one CTA per big pair), the entries missing from either
+//    child are queued and evaluated one shadow ray per thread, and each pair merges
+//    when cost = eps + cost(q) < tau * S_hat, eps = max |V_q - V_p I_q / I_p|.
+//  * Pass 2 (Sec. 5, Eq. 3): per slice one cluster of eight CTAs draws (column from
+//    the integer CDF of g or of given weights, row uniform) in rounds, keeps the
+//    first occurrence of every new entry in draw order, and stops at
+//    ceil(rate m' n') entries.
 //  * Entry evaluation: one thread per pass-2 entry (one shadow ray).
 #include <cooperative_groups.h>
 #include <math.h>
@@ -25,11 +27,6 @@ using namespace ltk;
 namespace {
 
 constexpr int kP1Threads = 512;
-constexpr int kPairLanes = 8;   // lanes per sibling-pair test of a large pair
-constexpr int kSmallPair = 16;  // pairs with at most this many rows are tested by one thread
-constexpr int kBigQueue = 4096;
-constexpr int kHugePair = 128;  // pairs with more rows are tested by the whole block
-constexpr int kP2Threads = 1024;
 constexpr int kMaxRowsPerNode = 64;
 constexpr int kMaxDraws = 1 << 16;
 constexpr int kMaxCut = 16384;
