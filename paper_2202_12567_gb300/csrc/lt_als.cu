@@ -1,14 +1,20 @@
 // Completion of the slices from their sampled entries and the factorised render.
 //
-//  * Omega build: per slice, the observed entries are placed in row-major (CSR) and
-//    column-major (CSC) order through two occupancy bitmaps; the position of an entry
-//    is a popcount of the bits before it, so the layout is deterministic.
+//  * Omega build: per slice, the observed entries are placed through two occupancy
+//    bitmaps (the position of an entry is a popcount of the bits before it, so the
+//    layout is deterministic) into a sliced layout per side for the lane-group ALS
+//    (lines sorted by entry count, warp tasks of 32 lanes, streams interleaved by
+//    chunks of 4) and, for ranks above 16, into CSR / CSC.
 //  * Masked ALS (the completion M_s ~= U_s V_s^T at rank r; Sec. 5 uses the factor
-//    form M = X Y): one group of G lanes (G = 8, 16 or 32 >= r) solves one row (or
-//    column).  Lane k owns row k of the r x r Gram matrix in registers; the factor
-//    row of every observed entry is broadcast with shuffles.  The ridge-regularised
-//    Gram is factored by an in-register Cholesky; when the float32 pivots spread
-//    beyond 1e6 the group repeats the row in float64.
+//    form M = X Y): up to rank 16 a line (a row of U or of V) belongs to a group of
+//    2^g lanes sized by its entry count; each lane accumulates its part of the Gram
+//    and right-hand side in registers from the slice's factor rows staged in shared
+//    memory, the group reduces with shuffles and its first lane adds the ridge
+//    lam_rel tr(G) / r, factors by Cholesky in float32 and solves; lines whose pivots
+//    spread beyond 1e6 are solved again in float64.  The half-step kernel is
+//    persistent: each CTA takes an equal share of all slices' warp tasks.  Above
+//    rank 16 a warp group holds a line's Gram (built on the tensor cores) row by row.
+//    The rank may differ per slice (factor rows keep the stride of the largest).
 //  * Render (Sec. 3 step 5): t_s = V_s^T w, pixel = max(0, u_i . t_s).
 #include <math.h>
 
