@@ -216,6 +216,23 @@ lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, const lt_sa
  * Cholesky with a float64 retry when min/max pivot^2 < 1e-6. */
 lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
                       float lam_rel, uint64_t seed, lt_factors* uv);
+/* Nonnegative completion of every slice by the alternating direction method of
+ * App. A, `iters` iterations (X step, Y step, Z, U, V, Lambda, Pi in the appendix's
+ * order) at rank r (uv->rank[s] per slice when given).  Readings: the Y step uses
+ * X^T Z; Lambda_{k+1} = Lambda_k + gamma alpha (X_{k+1} - U_{k+1}); P_Omega keeps
+ * the observed entries (Z = M there).  Penalties alpha = alpha_rel ||Y0||_F^2 / r and
+ * beta = alpha_rel ||X0||_F^2 / r from the start, constant over the iterations;
+ * 0 < gamma < 1.618 (the appendix's interval).  Start: Y0^T = the lt_complete start
+ * (Philox (k, j, slice, 3)), X0[i][k] = sqrt(mu / r) (0.5 + w / 2^32) with w from
+ * Philox (k, i, slice, 6), mu the slice's mean observed value; U0 = X0, V0 = Y0,
+ * Lambda0 = Pi0 = 0.  Writes X to uv->U ([m][r] in slice row order) and Y^T to uv->V
+ * ([S][C][r]), the layout lt_render reads; a slice with no entries or mean value
+ * <= 0 gets zero factors.  Float32 throughout; Z is never formed (only its observed
+ * part, from the factors).  Needs device scratch of 3 m r + 2 S C r floats besides
+ * the observed-entry layout.  LT_EINVAL for alpha_rel <= 0, gamma outside
+ * (0, 1.618), iters < 0 or r outside 1..32. */
+lt_status lt_complete_adm(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
+                          float alpha_rel, float gamma, uint64_t seed, lt_factors* uv);
 /* Per-slice rank rule: rank[s] = min(R, max(8, 8 ceil(n'_s / cols))), a multiple of 8
  * that grows with the slice's coarsened cut (n'_s after lt_sample_pass1). */
 lt_status lt_slice_ranks(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t R, int32_t cols,
@@ -308,10 +325,16 @@ typedef struct {
     float mix;
     int32_t rank_cols;    /* > 0: after pass 1 the frame sets uv->rank by lt_slice_ranks with
                              R = uv->r and cols = rank_cols (uv->rank must be given); 0: fixed */
+    int32_t completion;   /* LT_COMPLETE_ALS (lt_complete with als_iters, lam_rel) or
+                             LT_COMPLETE_ADM (lt_complete_adm with the three values below) */
+    int32_t adm_iters;
+    float adm_alpha_rel;
+    float adm_gamma;
 } lt_params;
+enum { LT_COMPLETE_ALS = 0, LT_COMPLETE_ADM = 1 };
 
 /* One frame as a sequence of launches on the context's stream: lt_sample_pass1,
- * lt_sample_pass2, lt_eval_entries, lt_complete (rank uv->r) and lt_render with
+ * lt_sample_pass2, lt_eval_entries, lt_complete or lt_complete_adm (rank uv->r) and lt_render with
  * w = NULL, all with `seed`.  It reads two setup-dependent sizes back from the
  * device, so it synchronises the stream twice. */
 lt_status lt_render_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed,

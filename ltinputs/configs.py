@@ -18,7 +18,14 @@ import copy
 #   rank      completion rank r (the paper's q, Sec. 5)
 #   als_iters fixed number of alternating least-squares sweeps
 #   lam_rel   ridge term relative to the mean Gram diagonal
+#   completion  "als" (masked ALS) or "adm" (the nonnegative ADM of App. A) with
+#             adm_iters iterations, penalties adm_alpha_rel times the start's mean
+#             Gram diagonal, and step gamma adm_gamma
 _BASE = dict(
+    completion="als",
+    adm_iters=100,
+    adm_alpha_rel=0.3,
+    adm_gamma=1.0,
     light_power=1.0,
     light_size=0.2,
     eps_cut=0.05,

@@ -11,7 +11,7 @@ import time
 
 import numpy as np
 
-from . import als, cut as cut_mod, pass1, pass2, render, shading, slices as slices_mod, tree as tree_mod
+from . import adm, als, cut as cut_mod, pass1, pass2, render, shading, slices as slices_mod, tree as tree_mod
 from .tree import node_scale
 
 
@@ -70,8 +70,12 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
         v2 = np.zeros(0)
     res = SliceResult(p1=p1, p2_rows=r2, p2_cols=c2, p2_vals=v2, U=None, V=None, hit_cap=hit_cap)
     rows, cols, vals = res.omega()
-    res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["als_iters"],
-                                      cfg["lam_rel"], seed, s)
+    if cfg.get("completion", "als") == "adm":
+        res.U, res.V = adm.complete_slice_adm(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["adm_iters"],
+                                              cfg["adm_alpha_rel"], cfg["adm_gamma"], seed, s)
+    else:
+        res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["als_iters"],
+                                          cfg["lam_rel"], seed, s)
     return res
 
 

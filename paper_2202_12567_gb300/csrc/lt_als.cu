@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "lt_internal.cuh"
+#include "lt_omega.cuh"
 
 using namespace ltk;
 
@@ -29,49 +30,6 @@ namespace {
 
 constexpr float kPivotRatio = 1e-6f;
 
-struct Omega {
-    int32_t* rp;        // [m + S]      row pointers, slice s rows at slice_off[s] + s
-    int32_t* cp;        // [S][C + 1]   column pointers
-    uint16_t* cidx;     // [off[S]]     CSR column of each entry
-    float* cval;        // [off[S]]
-    uint16_t* ridx;     // [off[S]]     CSC row of each entry
-    float* rval;        // [off[S]]
-    float* mu;          // [S] mean observed value
-    uint32_t* bm;       // row-major bitmaps
-    uint32_t* bt;       // column-major bitmaps
-    uint32_t* wr;       // per word of bm: set bits before it in its row
-    uint32_t* wc;       // per word of bt: set bits before it in its column
-    int64_t bm_stride, bt_stride;
-    int64_t* line_pfx;  // [S + 1] prefix of n'_s (V-step lines)
-    int32_t* rord;      // [m]          rows of each slice by decreasing entry count
-    int32_t* cord;      // [S][C]       columns of each slice by decreasing entry count
-    int32_t* rcls;      // [S][16]      per group-size class g: first sorted row, first warp task
-    int32_t* ccls;      // [S][16]      the same for the columns
-    // Sliced layout of the lane-group ALS (r <= 16), one per side: the entry streams
-    // of the 32 lanes of a warp task interleaved in chunks of 4, entry kk of lane l at
-    // base[s] + tb[t] + 128 (kk / 4) + 4 l + kk % 4, so that a lane reads 4 entries
-    // with one 8-byte and one 16-byte load and a warp's loads are coalesced.
-    int32_t* rpos;      // [m]          sorted position of each row
-    int32_t* cpos;      // [S][C]       sorted position of each column
-    int32_t* rtb;       // [S][tcap]    offset of each rows-side warp task in its slice's region
-    int32_t* ctb;       // [S][tcap]
-    int64_t* rbase;     // [S + 1]      region start of each slice, rows side ([S] = total)
-    int64_t* cbase;     // [S + 1]
-    uint16_t* sidx_r;   // [sell_cap]   column of each rows-side slot
-    float* sval_r;
-    uint16_t* sidx_c;   // [sell_cap]   row of each columns-side slot
-    float* sval_c;
-    int64_t sell_cap;
-    int tcap;
-    int lane_entries;   // class threshold (line_class)
-    bool sell;          // fill the sliced layout
-    bool csr;           // fill CSR / CSC (the warp-group ALS for r > 16)
-};
-
-// rank of slice s: rk[s] clamped to [1, R], or R when there are no per-slice ranks
-__device__ __forceinline__ int slice_rank(const int32_t* __restrict__ rk, int s, int R) {
-    return rk ? min(max(rk[s], 1), R) : R;
-}
 
 // Group-size classes of a line: class g gives a line of L entries G = 2^g lanes, so
 // that a lane takes at most about `lane_entries` of them (g = 0..5; a tuning value).
@@ -377,6 +335,7 @@ __global__ void k_om_scatter(lt_frame F, lt_samples smp, Omega om) {
             om.cval[o + rp[r] + kr] = v;
             om.ridx[o + cp[c] + kc] = (uint16_t)r;
             om.rval[o + cp[c] + kc] = v;
+            om.c2r[o + cp[c] + kc] = rp[r] + kr;
         }
         if (om.sell) {
             const int64_t pr = sell_slot(om.rcls + (int64_t)s * 16, om.rtb + (int64_t)s * om.tcap,
@@ -1149,39 +1108,20 @@ __global__ void k_slice_ranks(lt_samples smp, int S, int R, int cols, int32_t* _
     }
 }
 
-bool frame_ok2(const lt_frame* f) {
-    return f && f->slice_off && f->S > 0 && f->S <= 1024 && f->m > 0 && f->C >= 1 && f->max_rows >= 0 &&
-           f->max_rows <= 65535;
-}
-
 }  // namespace
 
-extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
-                                 float lam_rel, uint64_t seed, lt_factors* uv) {
-    if (!ctx || !frame_ok2(f) || !smp || !smp->key || !smp->val || !smp->off || !smp->cnt || !smp->ncol || !uv ||
-        !uv->U || !uv->V || uv->r < 1 || uv->r > 32 || iters < 0 || !(lam_rel >= 0.f))
-        return lt_fail(ctx, LT_EINVAL, "lt_complete: bad arguments");
-    cudaSetDevice(ctx->device);
+namespace ltk {
+
+lt_status omega_build(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int64_t E, bool sell, bool csr,
+                      Omega* omp) {
     const int S = f->S, C = f->C;
-    // The sampling capacity sizes the scratch; a captured frame reuses the recorded value.
-    int64_t E = 0;
-    if (ctx->use_plan) {
-        E = ctx->plan.entries;
-    } else {
-        LT_CUDA(ctx, cudaMemcpyAsync(&E, smp->off + S, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-        LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-        ctx->plan.entries = E;
-    }
+    constexpr int kOmParts = 8;
     const int64_t mr = std::max(f->max_rows, 1);
-    const int R = uv->r;            // stride of the factor rows, the largest rank
-    const int32_t* rk = uv->rank;   // per-slice ranks (NULL: R for every slice)
-    Omega om;
+    Omega& om = *omp;
     om.bm_stride = mr * ((C + 31) / 32);
     om.bt_stride = (int64_t)C * ((mr + 31) / 32);
-    // the lane-group ALS takes slices of rank <= 16 (sliced layout), the warp-group
-    // ALS the others (CSR / CSC); with per-slice ranks above 16 both run
-    om.sell = R <= 16 || rk != nullptr;
-    om.csr = R > 16;
+    om.sell = sell;
+    om.csr = csr;
     // Sliced layout capacity, le = lane_entries.  Per slice and side, for lines sorted
     // by count, the padding of a task is at most the entries of the task before it
     // (the first task of class g < 5 adds at most 32 le slots, of class 5 at most
@@ -1198,10 +1138,10 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const size_t t_sell = om.sell ? (size_t)S * om.tcap : 0;
     lt_status st;
     char* p = (char*)lt_scratch(ctx, SCR_OMEGA,
-                                (size_t)(f->m + S) * 4 + (size_t)S * (C + 1) * 4 + e_csr * 12 + e_sell * 12 + S * 8 +
+                                (size_t)(f->m + S) * 4 + (size_t)S * (C + 1) * 4 + e_csr * 16 + e_sell * 12 + S * 8 +
                                     (size_t)S * (om.bm_stride + om.bt_stride) * 8 + (S + 1) * 8 + (size_t)f->m * 8 +
                                     (size_t)S * C * 8 + (size_t)S * 128 + t_sell * 8 + (size_t)(S + 1) * 16 +
-                                    32 * 256,
+                                    (size_t)S * kOmParts * 4 + 34 * 256,
                                 &st);
     if (!p) return st;
     auto take = [&](size_t nbytes) {
@@ -1215,6 +1155,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.cval = (float*)take(e_csr * 4);
     om.ridx = (uint16_t*)take(e_csr * 2);
     om.rval = (float*)take(e_csr * 4);
+    om.c2r = (int32_t*)take(e_csr * 4);
     om.mu = (float*)take(S * 4);
     om.bm = (uint32_t*)take((size_t)S * om.bm_stride * 4);
     om.bt = (uint32_t*)take((size_t)S * om.bt_stride * 4);
@@ -1235,18 +1176,9 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     om.sval_r = (float*)take(e_sell * 4);
     om.sidx_c = (uint16_t*)take(e_sell * 2);
     om.sval_c = (float*)take(e_sell * 4);
+    float* part = (float*)take((size_t)S * kOmParts * 4);  // partial sums of the observed values
     if ((size_t)(p - (char*)ctx->scr[SCR_OMEGA]) > ctx->scr_size[SCR_OMEGA])
-        return lt_fail(ctx, LT_ENOMEM, "lt_complete: Omega layout overflow");
-    const int RP = R <= 8 ? 8 : 16;  // lane-group kernel for ranks up to RP
-    // per half-step retry counters, the float64 count, the mean partials
-    constexpr int kOmParts = 8;
-    const int nq = std::max(1, 2 * iters);
-    char* sp = (char*)lt_scratch(ctx, SCR_ALS, (size_t)(nq + 64) * 4 + (size_t)S * kOmParts * 4 + 512, &st);
-    if (!sp) return st;
-    int32_t* n64 = (int32_t*)sp;
-    int32_t* qcount = n64 + 64;
-    float* part = (float*)(sp + (((size_t)(nq + 64) * 4 + 255) & ~(size_t)255));
-    LT_CUDA(ctx, cudaMemsetAsync(n64, 0, (size_t)(nq + 64) * 4, ctx->stream));
+        return lt_fail(ctx, LT_ENOMEM, "omega_build: layout overflow");
     const int nsm = ctx->num_sms;
     k_om_clear<<<dim3(std::max(1, 2 * nsm / S), S), 256, 0, ctx->stream>>>(*f, *smp, om);
     LT_LAUNCH_CHECK(ctx, "k_om_clear");
@@ -1264,6 +1196,44 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     LT_LAUNCH_CHECK(ctx, "k_om_scatter");
     k_line_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, S, om.line_pfx);
     LT_LAUNCH_CHECK(ctx, "k_line_prefix");
+    return LT_OK;
+}
+
+}  // namespace ltk
+
+extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
+                                 float lam_rel, uint64_t seed, lt_factors* uv) {
+    if (!ctx || !frame_ok2(f) || !smp || !smp->key || !smp->val || !smp->off || !smp->cnt || !smp->ncol || !uv ||
+        !uv->U || !uv->V || uv->r < 1 || uv->r > 32 || iters < 0 || !(lam_rel >= 0.f))
+        return lt_fail(ctx, LT_EINVAL, "lt_complete: bad arguments");
+    cudaSetDevice(ctx->device);
+    const int S = f->S, C = f->C;
+    // The sampling capacity sizes the scratch; a captured frame reuses the recorded value.
+    int64_t E = 0;
+    if (ctx->use_plan) {
+        E = ctx->plan.entries;
+    } else {
+        LT_CUDA(ctx, cudaMemcpyAsync(&E, smp->off + S, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+        LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        ctx->plan.entries = E;
+    }
+    const int64_t mr = std::max(f->max_rows, 1);
+    const int R = uv->r;            // stride of the factor rows, the largest rank
+    const int32_t* rk = uv->rank;   // per-slice ranks (NULL: R for every slice)
+    // the lane-group ALS takes slices of rank <= 16 (sliced layout), the warp-group
+    // ALS the others (CSR / CSC); with per-slice ranks above 16 both run
+    Omega om;
+    lt_status st = omega_build(ctx, f, smp, E, R <= 16 || rk != nullptr, R > 16, &om);
+    if (st != LT_OK) return st;
+    const int RP = R <= 8 ? 8 : 16;  // lane-group kernel for ranks up to RP
+    // per half-step retry counters and the float64 count
+    const int nq = std::max(1, 2 * iters);
+    char* sp = (char*)lt_scratch(ctx, SCR_ALS, (size_t)(nq + 64) * 4 + 256, &st);
+    if (!sp) return st;
+    int32_t* n64 = (int32_t*)sp;
+    int32_t* qcount = n64 + 64;
+    LT_CUDA(ctx, cudaMemsetAsync(n64, 0, (size_t)(nq + 64) * 4, ctx->stream));
+    const int nsm = ctx->num_sms;
     k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, R, rk, seed_ref(ctx, seed), uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
     // lane-group kernel: one thread (group) per line; one 256-thread CTA per SM stages

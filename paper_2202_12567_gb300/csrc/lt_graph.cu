@@ -24,7 +24,10 @@ __global__ void k_set_seed(uint64_t* dst, uint64_t seed) { *dst = seed; }
 
 bool params_ok(const lt_params* p) {
     return p && p->rate1 >= 0.f && p->tau >= 0.f && p->d_min >= 0.f && p->rate >= 0.f && p->als_iters >= 0 &&
-           p->lam_rel >= 0.f && (!p->proposal || (p->mix >= 0.f && p->mix <= 1.f)) && p->rank_cols >= 0;
+           p->lam_rel >= 0.f && (!p->proposal || (p->mix >= 0.f && p->mix <= 1.f)) && p->rank_cols >= 0 &&
+           (p->completion == LT_COMPLETE_ALS ||
+            (p->completion == LT_COMPLETE_ADM && p->adm_iters >= 0 && p->adm_alpha_rel > 0.f &&
+             p->adm_gamma > 0.f && p->adm_gamma < 1.618f));
 }
 
 lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed, lt_samples* smp,
@@ -58,7 +61,9 @@ lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t
     if (st != LT_OK) return st;
     st = lt_eval_entries(ctx, f, p->d_min, smp);
     if (st != LT_OK) return st;
-    st = lt_complete(ctx, f, smp, p->als_iters, p->lam_rel, seed, uv);
+    st = p->completion == LT_COMPLETE_ADM
+             ? lt_complete_adm(ctx, f, smp, p->adm_iters, p->adm_alpha_rel, p->adm_gamma, seed, uv)
+             : lt_complete(ctx, f, smp, p->als_iters, p->lam_rel, seed, uv);
     if (st != LT_OK) return st;
     return lt_render(ctx, f, smp, uv, nullptr, row_perm, img);
 }

@@ -19,7 +19,7 @@ constexpr float kRayOffset = 1e-4f;
 constexpr float kTMin = 1e-4f;
 constexpr float kTMax = 1.0f - 1e-4f;
 constexpr float kInvPi = 0.318309886183790672f;
-constexpr uint32_t kTagPass1 = 1, kTagPass2 = 2, kTagAlsInit = 3;
+constexpr uint32_t kTagPass1 = 1, kTagPass2 = 2, kTagAlsInit = 3, kTagAdmInit = 6;
 
 // The seed of a frame: passed by value, or read from a device word so that one
 // captured graph replays every seed.
@@ -363,6 +363,7 @@ enum ScratchSlot {
     SCR_PROPOSAL_G,     // logits, their gradient and per-CTA weight gradients
     SCR_FRAME_PROP,     // features, groups, logits and weights of a frame's proposal
     SCR_P2_CDF,         // pass-2 integer CDF of every slice
+    SCR_ADM,            // second X buffer, U, Lambda, V and Pi of the ADM completion
     SCR_NSLOTS
 };
 

@@ -57,7 +57,11 @@ class lt_factors(ctypes.Structure):
 
 class lt_params(ctypes.Structure):
     _fields_ = [("rate1", _f32), ("tau", _f32), ("d_min", _f32), ("rate", _f32), ("als_iters", _i32),
-                ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32), ("rank_cols", _i32)]
+                ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32), ("rank_cols", _i32),
+                ("completion", _i32), ("adm_iters", _i32), ("adm_alpha_rel", _f32), ("adm_gamma", _f32)]
+
+
+COMPLETE_ALS, COMPLETE_ADM = 0, 1
 
 
 MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 32, 64, 10497
@@ -93,6 +97,8 @@ _SIGS = {
     "lt_eval_entries_noalloc": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples)]),
     "lt_complete": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _u64,
                            ctypes.POINTER(lt_factors)]),
+    "lt_complete_adm": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _f32, _u64,
+                               ctypes.POINTER(lt_factors)]),
     "lt_render": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p,
                          _p, _p]),
     "lt_render_frame": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_params), _u64,
@@ -400,6 +406,12 @@ def lt_complete(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, la
                                                   iters, lam_rel, seed, ctypes.byref(uv.struct())))
 
 
+def lt_complete_adm(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, alpha_rel, gamma, seed):
+    ctx._check("lt_complete_adm", ctx.lib.lt_complete_adm(ctx.h, ctypes.byref(frame.struct()),
+                                                          ctypes.byref(smp.struct()), iters, alpha_rel, gamma, seed,
+                                                          ctypes.byref(uv.struct())))
+
+
 def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, img, w=None):
     ctx._check("lt_render", ctx.lib.lt_render(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
                                               ctypes.byref(uv.struct()), _ptr(w), _ptr(row_perm), _ptr(img)))
@@ -407,9 +419,13 @@ def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, i
 
 def params(cfg: dict, weights=None, proposal=None, mix: float = 0.8) -> lt_params:
     """lt_params of a configuration dict (rate1, tau, d_min, rate, als_iters, lam_rel,
-    rank_cols: 0 or absent = one rank per frame)."""
+    rank_cols: 0 or absent = one rank per frame; completion "als" (default) or "adm"
+    with adm_iters, adm_alpha_rel, adm_gamma)."""
+    adm = cfg.get("completion", "als") == "adm"
     return lt_params(cfg["rate1"], cfg["tau"], cfg["d_min"], cfg["rate"], cfg["als_iters"], cfg["lam_rel"],
-                     _ptr(weights), _ptr(proposal), mix, int(cfg.get("rank_cols", 0)))
+                     _ptr(weights), _ptr(proposal), mix, int(cfg.get("rank_cols", 0)),
+                     COMPLETE_ADM if adm else COMPLETE_ALS, int(cfg.get("adm_iters", 100)),
+                     float(cfg.get("adm_alpha_rel", 0.3)), float(cfg.get("adm_gamma", 1.0)))
 
 
 def lt_slice_ranks(ctx: Context, frame: Frame, smp: Samples, R: int, cols: int, rank=None):

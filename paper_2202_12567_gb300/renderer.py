@@ -82,7 +82,11 @@ class Renderer:
         c = self.cfg
         if int(c.get("rank_cols", 0)) > 0:  # per-slice ranks from the coarsened cut
             lt.lt_slice_ranks(self.ctx, self.frame, self.smp, c["rank"], c["rank_cols"], self.uv.rank)
-        lt.lt_complete(self.ctx, self.frame, self.smp, self.uv, c["als_iters"], c["lam_rel"], seed)
+        if c.get("completion", "als") == "adm":  # nonnegative completion (App. A)
+            lt.lt_complete_adm(self.ctx, self.frame, self.smp, self.uv, c["adm_iters"], c["adm_alpha_rel"],
+                               c["adm_gamma"], seed)
+        else:
+            lt.lt_complete(self.ctx, self.frame, self.smp, self.uv, c["als_iters"], c["lam_rel"], seed)
 
     def render_image(self, w=None):
         lt.lt_render(self.ctx, self.frame, self.smp, self.uv, self.row_perm, self.img, w)
