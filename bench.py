@@ -318,7 +318,7 @@ def run_ours(args):
     same_as_graph = bool(torch.equal(R.img, img_g))
     # ALS half-step on the launching stream: complete at K sweeps minus at 0 sweeps
     c_ms = {}
-    for iters in (cfg["als_iters"], 0):
+    for iters in (0, cfg["als_iters"]):
         xs = []
         for k in range(max(3, args.steps // 4)):
             a = torch.cuda.Event(enable_timing=True)
@@ -330,6 +330,24 @@ def run_ours(args):
             xs.append(a.elapsed_time(b))
         c_ms[iters] = statistics.median(xs[1:])
     half_ms = (c_ms[cfg["als_iters"]] - c_ms[0]) / (2 * cfg["als_iters"])
+    img_als = torch.empty_like(R.img)
+    lt.lt_render(ctx, R.frame, R.smp, R.uv, R.row_perm, img_als)
+    # the nonnegative ADM completion of App. A on the same samples (one launch runs
+    # every iteration; the start alone is timed as 0 iterations)
+    a_ms = {}
+    for iters in (0, cfg["adm_iters"]):
+        xs = []
+        for k in range(4):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            lt.lt_complete_adm(ctx, R.frame, R.smp, R.uv, iters, cfg["adm_alpha_rel"], cfg["adm_gamma"], seed0)
+            b.record()
+            torch.cuda.synchronize()
+            xs.append(a.elapsed_time(b))
+        a_ms[iters] = statistics.median(xs[1:])
+    img_adm = torch.empty_like(R.img)
+    lt.lt_render(ctx, R.frame, R.smp, R.uv, R.row_perm, img_adm)
     clk = clocks.stop()
     lt.lt_sync(ctx)
 
@@ -348,6 +366,12 @@ def run_ours(args):
     rel = float(torch.linalg.norm(img.double() - bf.double()) / nbf)
     rel_g = float(torch.linalg.norm(img_g.double() - bf.double()) / nbf)
     rays_per_px = float(R.rays()) / R.frame.m
+    adm = dict(iters=cfg["adm_iters"], alpha_rel=cfg["adm_alpha_rel"], gamma=cfg["adm_gamma"],
+               completion_ms=round(a_ms[cfg["adm_iters"]], 3),
+               ms_per_iteration=round((a_ms[cfg["adm_iters"]] - a_ms[0]) / max(cfg["adm_iters"], 1), 4),
+               rel_rmse=round(float(torch.linalg.norm(img_adm.double() - bf.double()) / nbf), 5),
+               als_completion_ms=round(c_ms[cfg["als_iters"]], 3),
+               als_rel_rmse_same_samples=round(float(torch.linalg.norm(img_als.double() - bf.double()) / nbf), 5))
 
     # end to end through the C ABI from pinned host buffers: points and VPLs in, image out
     pts_h = torch.from_numpy(sc.points).pin_memory()
@@ -395,6 +419,7 @@ def run_ours(args):
                             plain_equals_graph_bitwise=same_as_graph,
                             tuning=dict(key=tune_key, values=tune_values, from_cache=tune_cached),
                             eval_roofline=roof_eval,
+                            adm_completion=adm,
                             setup_ms=round(setup_ms, 1),
                             stage_ms=dict(zip(["pass1", "pass2", "eval", "complete", "render"],
                                               [round(x, 4) for x in stage_ms.tolist()]))),

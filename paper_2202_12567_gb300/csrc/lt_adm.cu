@@ -56,11 +56,14 @@ struct AdmArgs {
     float* Vp;   // [S][C][R]  V^T
     float* Pi;   // [S][C][R]  Pi^T
     float* S;    // [E]  residual m_ij - x_i . y_j of each observed entry (CSR order)
+    const int32_t* ordr;  // [m]        rows of each slice ordered by class (k_adm_order)
+    const int32_t* ordc;  // [S][C]     columns of each slice ordered by class
+    const int32_t* ncls;  // [S][2][8]  lines per class, rows then columns
     int R;
     const int32_t* rk;
     int iters;
     float alpha_rel, gamma;
-    int stage_cols;  // Y is staged in shared memory when n'_s <= stage_cols
+    int stage_cap;   // factor rows the shared buffer holds: Y (X) is staged when n'_s (m'_s) fits
 };
 
 // a factor row of stride R into RP registers (zeros beyond R), from L2
@@ -78,22 +81,95 @@ __device__ __forceinline__ void load_row_cg(const float* __restrict__ p, int R, 
     }
 }
 
-template <int RP>
-__device__ __forceinline__ void load_row_smem(const float* __restrict__ p, float (&v)[RP]) {
-#pragma unroll
-    for (int c = 0; c < RP; c += 4) {
-        const float4 q = *reinterpret_cast<const float4*>(p + c);
-        v[c] = q.x, v[c + 1] = q.y, v[c + 2] = q.z, v[c + 3] = q.w;
+
+// Group-size class of a line of `len` entries: the line gets G = 2^g lanes, the
+// smallest with at most kAdmLaneEntries entries per lane (g <= 5).
+constexpr int kAdmLaneEntries = 32;
+constexpr int kAdmClasses = 6;
+
+__device__ __forceinline__ int adm_class(int len) {
+    int g = 0;
+    while (g < kAdmClasses - 1 && len > (kAdmLaneEntries << g)) ++g;
+    return g;
+}
+
+// Lines of every slice and side ordered by class, largest class first and by line
+// index within a class (a stable counting sort, so the order is deterministic), and
+// the count of each class.  Block (s, side): side 0 the rows, 1 the columns.
+__global__ void k_adm_order(lt_frame F, lt_samples smp, Omega om, int32_t* __restrict__ ordr,
+                            int32_t* __restrict__ ordc, int32_t* __restrict__ ncls) {
+    __shared__ int32_t ws[32];
+    __shared__ int32_t cnt[kAdmClasses], base[kAdmClasses];
+    const int s = blockIdx.x, side = blockIdx.y;
+    const int row0 = F.slice_off[s];
+    const int n = side ? smp.ncol[s] : F.slice_off[s + 1] - row0;
+    const int32_t* ptr = side ? om.cp + (int64_t)s * (F.C + 1) : om.rp + row0 + s;
+    int32_t* ord = side ? ordc + (int64_t)s * F.C : ordr + row0;
+    if (threadIdx.x < kAdmClasses) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[adm_class(ptr[i + 1] - ptr[i])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int P = 0;
+        for (int g = kAdmClasses - 1; g >= 0; --g) {
+            base[g] = P;
+            P += cnt[g];
+            ncls[((int64_t)s * 2 + side) * 8 + g] = cnt[g];
+        }
+    }
+    __syncthreads();
+    for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const int g = i < n ? adm_class(ptr[i + 1] - ptr[i]) : -1;
+        for (int c = kAdmClasses - 1; c >= 0; --c) {
+            int32_t tot;
+            const int32_t before = block_exclusive_scan<int32_t>(g == c ? 1 : 0, ws, &tot);
+            if (g == c) ord[base[c] + before] = i;
+            __syncthreads();
+            if (threadIdx.x == 0) base[c] += tot;
+            __syncthreads();
+        }
     }
 }
 
-// group size for lines of mean length L: the smallest power of two in [2, 32] with
-// at most about 6 entries per lane
-__device__ __forceinline__ int group_size(int64_t entries, int lines) {
-    const int64_t L = lines > 0 ? (entries + lines - 1) / lines : 0;
-    int G = 2;
-    while (G < 32 && (int64_t)G * 6 < L) G <<= 1;
-    return G;
+// The lines of one side that a CTA (rank k of K) takes: the class-g lines at sorted
+// positions pos0[g] + k + K q, q < n[g], in warp tasks of 32 / 2^g lines, tasks of
+// the largest class first.
+struct AdmSched {
+    int n[kAdmClasses], pos0[kAdmClasses], t0[kAdmClasses], tend[kAdmClasses];
+    int lines, tasks;
+};
+
+__device__ __forceinline__ void make_sched(const int32_t* __restrict__ cnt, int k, int K, AdmSched& sc) {
+    int P = 0, T = 0, L = 0;
+    for (int g = kAdmClasses - 1; g >= 0; --g) {
+        const int c = cnt[g];
+        sc.pos0[g] = P;
+        P += c;
+        sc.n[g] = c > k ? (c - k + K - 1) / K : 0;
+        L += sc.n[g];
+        sc.t0[g] = T;
+        T += (sc.n[g] + (32 >> g) - 1) >> (5 - g);
+        sc.tend[g] = T;
+    }
+    sc.lines = L;
+    sc.tasks = T;
+}
+
+// sorted position of the CTA's local line l (0 <= l < sc.lines; classes in task order)
+__device__ __forceinline__ int sched_pos(const AdmSched& sc, int l, int k, int K) {
+    int g = kAdmClasses - 1;
+    while (l >= sc.n[g]) l -= sc.n[g--];
+    return sc.pos0[g] + k + K * l;
+}
+
+// Offset in shared memory of float4 chunk q of staged factor row j: the chunk index
+// is XOR-swizzled by the row's place in its 128-byte bank line, so that a warp
+// gathering chunk q of random rows spreads over all banks.
+template <int RP>
+__device__ __forceinline__ int sy_chunk(int j, int q) {
+    constexpr int CPR = RP / 4, RPL = CPR >= 8 ? 1 : 8 / CPR;
+    return j * RP + 4 * (q ^ ((j / RPL) % CPR));
 }
 
 // Inverse of the symmetric positive definite M + add I (RP x RP, row-major in shared
@@ -168,19 +244,19 @@ __device__ __forceinline__ void tile_gram(const float* __restrict__ N, const flo
     }
 }
 
-// g1 += N^T N and, when O is given, g2 += N^T O over the n factor rows of stride R
-// that start at N and O, staged through `buf` (2 kAdmChunk RP floats of shared
-// memory) in chunks; every thread of the CTA calls it
-template <int RP, int NE>
-__device__ void gram_rows(const float* N, const float* O, int n, int R, float* __restrict__ buf, float (&g1)[NE],
-                          float (&g2)[NE]) {
+// g1 += N^T N and, when O is given, g2 += N^T O over n factor rows of stride R (row
+// l at N + line(l) R), staged through `buf` (2 kAdmChunk RP floats of shared memory)
+// in chunks; every thread of the CTA calls it
+template <int RP, int NE, class Line>
+__device__ void gram_rows(const float* N, const float* O, int n, int R, Line line, float* __restrict__ buf,
+                          float (&g1)[NE], float (&g2)[NE]) {
     float* bn = buf;
     float* bo = buf + kAdmChunk * RP;
     for (int base = 0; base < n; base += kAdmChunk) {
         const int nt = min(kAdmChunk, n - base);
         for (int e = threadIdx.x; e < nt * RP; e += kAdmThreads) {
             const int i = e / RP, c = e % RP;
-            const int64_t at = (int64_t)(base + i) * R + c;
+            const int64_t at = (int64_t)line(base + i) * R + c;
             bn[e] = c < R ? __ldcg(N + at) : 0.f;
             if (O) bo[e] = c < R ? __ldcg(O + at) : 0.f;
         }
@@ -224,13 +300,39 @@ __device__ __forceinline__ void group_reduce(float (&acc)[RP], int G, unsigned g
     }
 }
 
+// stage n factor rows of stride R into shared memory, swizzled
 template <int RP>
-__device__ __forceinline__ void load_y(bool staged, const float* sY, const float* Yb, int j, int R, float (&y)[RP]) {
-    if (staged)
-        load_row_smem<RP>(sY + j * RP, y);
-    else
-        load_row_cg<RP>(Yb + (int64_t)j * R, R, y);
+__device__ __forceinline__ void stage_rows(float* sm, const float* src, int n, int R) {
+    for (int e = threadIdx.x; e < n * RP; e += kAdmThreads) {
+        const int j = e / RP, c = e % RP;
+        sm[sy_chunk<RP>(j, c >> 2) + (c & 3)] = c < R ? src[(int64_t)j * R + c] : 0.f;
+    }
 }
+
+// a factor row from the staged copy or from global memory (plain loads: every
+// reader is ordered after the writer by a cluster or CTA barrier)
+template <int RP>
+__device__ __forceinline__ void load_f(bool staged, const float* sm, const float* src, int j, int R,
+                                       float (&y)[RP]) {
+    if (staged) {
+#pragma unroll
+        for (int q = 0; q < RP / 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(sm + sy_chunk<RP>(j, q));
+            y[4 * q] = t.x, y[4 * q + 1] = t.y, y[4 * q + 2] = t.z, y[4 * q + 3] = t.w;
+        }
+    } else if (R == RP) {
+#pragma unroll
+        for (int q = 0; q < RP / 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(src + (int64_t)j * R + 4 * q);
+            y[4 * q] = t.x, y[4 * q + 1] = t.y, y[4 * q + 2] = t.z, y[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < RP; ++c) y[c] = c < R ? src[(int64_t)j * R + c] : 0.f;
+    }
+}
+
+constexpr int kAdmBatch = 8;  // entries whose indices a lane loads at once
 
 template <int RP>
 __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples smp, Omega om, AdmArgs a, SeedRef sr) {
@@ -261,13 +363,13 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
     float* Yb = a.Y + (int64_t)s * F.C * R;
     float* Vb = a.Vp + (int64_t)s * F.C * R;
     float* Pb = a.Pi + (int64_t)s * F.C * R;
-    float* Sr = a.S + o;  // residual of each observed entry, CSR order
+    float* Sr = a.S + o;  // residual of each observed entry, CSC order
     const int32_t* rp = om.rp + row0 + s;
     const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
     const uint16_t* cidx = om.cidx + o;
     const float* cval = om.cval + o;
     const uint16_t* ridx = om.ridx + o;
-    const int32_t* c2r = om.c2r + o;
+    const int32_t* r2c = om.r2c + o;
 
     if (ne == 0 || !(mu > 0.f)) {
         // nothing observed, or an all-zero slice: the zero factors fit
@@ -279,7 +381,7 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
     }
     const uint64_t seed = sr.get();
     const float amp = sqrtf(mu / (float)r);
-    const bool staged = ns <= a.stage_cols;
+    const bool staged = ns <= a.stage_cap, staged_x = ms <= a.stage_cap;
 
     // ---- start: Y0 as the ALS start (Philox (k, j, slice, 3)), X0 from (k, i, slice, 6);
     // U0 = X0, V0 = Y0, Lambda0 = Pi0 = 0; the CTA's parts of Y0 Y0^T and ||X0||^2
@@ -313,7 +415,7 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
     float gA[NE], gB[NE], gC[NE];
 #pragma unroll
     for (int q = 0; q < NE; ++q) gA[q] = 0.f;
-    gram_rows<RP, NE>(Yb + (int64_t)clo * R, nullptr, chi - clo, R, sY, gA, gA);
+    gram_rows<RP, NE>(Yb, nullptr, chi - clo, R, [&](int l) { return clo + l; }, sY, gA, gA);
     store_part<RP, NE>(sPartA, gA);
     if (tid == 0) sPartA[RP * RP] = ssx;
     __threadfence();
@@ -329,77 +431,84 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
     __syncthreads();
     const float alpha = sAB[0], beta = sAB[1], gamma = a.gamma;
     if (tid < 32) gj_inverse<RP>(sM, alpha, sInv, tid);
-    if (staged)
-        for (int e = tid; e < ns * RP; e += kAdmThreads) {
-            const int j = e / RP, c = e % RP;
-            sY[e] = c < R ? __ldcg(Yb + (int64_t)j * R + c) : 0.f;
-        }
+    if (staged) stage_rows<RP>(sY, Yb, ns, R);
     __syncthreads();
 
-    const int Gx = group_size(ne, ms), Gy = group_size(ne, ns);
+    __shared__ AdmSched shr, shc;  // the CTA's rows and columns
+    if (tid == 0) {
+        make_sched(a.ncls + (int64_t)s * 16, k, K, shr);
+        make_sched(a.ncls + (int64_t)s * 16 + 8, k, K, shc);
+    }
+    __syncthreads();
+    const int32_t* ordr = a.ordr + row0;
+    const int32_t* ordc = a.ordc + (int64_t)s * F.C;
+    const int warp = tid >> 5, lane32 = tid & 31;
     for (int it = 0; it < a.iters; ++it) {
         const float* Xc = (it & 1) ? a.X1 : a.X0;  // X_k
         float* Xn = (it & 1) ? a.X0 : a.X1;        // X_{k+1}
-        // ---- X step: a group of Gx lanes per row, no barrier between rows ----------
-        {
-            const int G = Gx, ng = kAdmThreads / G, lane = tid % G;
-            const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
-            for (int i = rlo + tid / G; i < rhi; i += ng) {
-                const int64_t row = (int64_t)(row0 + i) * R;
-                float xo[RP], acc[RP];
-                load_row_cg<RP>(Xc + row, R, xo);
+        // ---- X step: a warp task = 32 / G rows of one class, G lanes per row -----------
+        for (int tau = warp; tau < shr.tasks; tau += kAdmThreads / 32) {
+            int g = kAdmClasses - 1;
+            while (tau >= shr.tend[g]) --g;
+            const int G = 1 << g, lane = lane32 & (G - 1);
+            const int q = (tau - shr.t0[g]) * (32 >> g) + (lane32 >> g);
+            if (q >= shr.n[g]) continue;  // a whole group leaves together
+            const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane32 & ~(G - 1)));
+            const int i = ordr[shr.pos0[g] + k + K * q];
+            const int64_t row = (int64_t)(row0 + i) * R;
+            float xo[RP], acc[RP];
+            load_row_cg<RP>(Xc + row, R, xo);
 #pragma unroll
-                for (int c = 0; c < RP; ++c) acc[c] = 0.f;
-                const int e1 = rp[i + 1];
-                int e = rp[i] + lane;
-                for (; e + G < e1; e += 2 * G) {  // two entries in flight
-                    const int j0 = cidx[e], j1 = cidx[e + G];
-                    float d0 = cval[e], d1 = cval[e + G];
-                    float y0[RP], y1[RP];
-                    load_y<RP>(staged, sY, Yb, j0, R, y0);
-                    load_y<RP>(staged, sY, Yb, j1, R, y1);
+            for (int c = 0; c < RP; ++c) acc[c] = 0.f;
+            const int e1 = rp[i + 1];
+            for (int e0 = rp[i] + lane; e0 < e1; e0 += kAdmBatch * G) {
+                int jj[kAdmBatch], ss[kAdmBatch];
+                float mm[kAdmBatch];
 #pragma unroll
-                    for (int c = 0; c < RP; ++c) {
-                        d0 = fmaf(-xo[c], y0[c], d0);
-                        d1 = fmaf(-xo[c], y1[c], d1);
-                    }
-                    Sr[e] = d0;
-                    Sr[e + G] = d1;
-#pragma unroll
-                    for (int c = 0; c < RP; ++c) acc[c] = fmaf(d1, y1[c], fmaf(d0, y0[c], acc[c]));
+                for (int u = 0; u < kAdmBatch; ++u) {
+                    const int e = e0 + u * G;
+                    jj[u] = e < e1 ? cidx[e] : -1;
+                    mm[u] = e < e1 ? cval[e] : 0.f;
+                    ss[u] = e < e1 ? r2c[e] : 0;
                 }
-                if (e < e1) {
-                    float y0[RP];
-                    load_y<RP>(staged, sY, Yb, cidx[e], R, y0);
-                    float d0 = cval[e];
 #pragma unroll
-                    for (int c = 0; c < RP; ++c) d0 = fmaf(-xo[c], y0[c], d0);
-                    Sr[e] = d0;
+                for (int u = 0; u < kAdmBatch; ++u) {
+                    if (jj[u] < 0) break;
+                    float y[RP];
+                    load_f<RP>(staged, sY, Yb, jj[u], R, y);
+                    float d = mm[u];
 #pragma unroll
-                    for (int c = 0; c < RP; ++c) acc[c] = fmaf(d0, y0[c], acc[c]);
-                }
-                // the lane that owns component c adds alpha (u_c - x_c) - lambda_c
+                    for (int c = 0; c < RP; ++c) d = fmaf(-xo[c], y[c], d);
+                    Sr[ss[u]] = d;
 #pragma unroll
-                for (int c = 0; c < RP; ++c)
-                    if (c < R && (c & (G - 1)) == lane)
-                        acc[c] += fmaf(alpha, __ldcg(a.Up + row + c) - xo[c], -__ldcg(a.Lam + row + c));
-                group_reduce<RP>(acc, G, gmask);
-                for (int c = lane; c < R; c += G) {
-                    float v = __ldcg(Xc + row + c);
-#pragma unroll
-                    for (int q = 0; q < RP; ++q) v = fmaf(acc[q], sInv[q * RP + c], v);
-                    const float lam = __ldcg(a.Lam + row + c);
-                    const float u = fmaxf(0.f, v + lam / alpha);
-                    Xn[row + c] = v;
-                    a.Up[row + c] = u;
-                    a.Lam[row + c] = lam + gamma * alpha * (v - u);
+                    for (int c = 0; c < RP; ++c) acc[c] = fmaf(d, y[c], acc[c]);
                 }
             }
-            __syncthreads();  // the CTA's new rows are written; sY is free
+            if (lane == 0) {  // alpha (U_k - X_k) - Lambda_k, once per row
+                float u[RP], lm[RP];
+                load_row_cg<RP>(a.Up + row, R, u);
+                load_row_cg<RP>(a.Lam + row, R, lm);
+#pragma unroll
+                for (int c = 0; c < RP; ++c) acc[c] += fmaf(alpha, u[c] - xo[c], -lm[c]);
+            }
+            group_reduce<RP>(acc, G, gmask);
+            for (int c = lane; c < R; c += G) {
+                float v = __ldcg(Xc + row + c);
+#pragma unroll
+                for (int q2 = 0; q2 < RP; ++q2) v = fmaf(acc[q2], sInv[q2 * RP + c], v);
+                const float lam = __ldcg(a.Lam + row + c);
+                const float u = fmaxf(0.f, v + lam / alpha);
+                Xn[row + c] = v;
+                a.Up[row + c] = u;
+                a.Lam[row + c] = lam + gamma * alpha * (v - u);
+            }
+        }
+        __syncthreads();  // the CTA's new rows are written; sY is free
+        {
 #pragma unroll
             for (int q = 0; q < NE; ++q) gB[q] = gC[q] = 0.f;
-            gram_rows<RP, NE>(Xn + (int64_t)(row0 + rlo) * R, Xc + (int64_t)(row0 + rlo) * R, rhi - rlo, R, sY, gB,
-                              gC);
+            auto line = [&](int l) { return row0 + ordr[sched_pos(shr, l, k, K)]; };
+            gram_rows<RP, NE>(Xn, Xc, shr.lines, R, line, sY, gB, gC);
             store_part<RP, NE>(sPartBC, gB);
             store_part<RP, NE>(sPartBC + RP * RP, gC);
         }
@@ -418,57 +527,69 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
             sD[e] = t;
         }
         __syncthreads();
-        // ---- Y step: a group of Gy lanes per column -----------------------------------
-        {
-            const int G = Gy, ng = kAdmThreads / G, lane = tid % G;
-            const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((tid & 31) & ~(G - 1)));
-            for (int j = clo + tid / G; j < chi; j += ng) {
-                const int64_t col = (int64_t)j * R;
-                float yo[RP], acc[RP];
-                load_row_cg<RP>(Yb + col, R, yo);
+        if (staged_x) stage_rows<RP>(sY, Xn + (int64_t)row0 * R, ms, R);
+        __syncthreads();
+        // ---- Y step: a warp task = 32 / G columns of one class --------------------------
+        for (int tau = warp; tau < shc.tasks; tau += kAdmThreads / 32) {
+            int g = kAdmClasses - 1;
+            while (tau >= shc.tend[g]) --g;
+            const int G = 1 << g, lane = lane32 & (G - 1);
+            const int q = (tau - shc.t0[g]) * (32 >> g) + (lane32 >> g);
+            if (q >= shc.n[g]) continue;
+            const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane32 & ~(G - 1)));
+            const int j = ordc[shc.pos0[g] + k + K * q];
+            const int64_t col = (int64_t)j * R;
+            float yo[RP], acc[RP];
+            load_row_cg<RP>(Yb + col, R, yo);
 #pragma unroll
-                for (int c = 0; c < RP; ++c) acc[c] = 0.f;
-                const int e1 = cp[j + 1];
-                int e = cp[j] + lane;
-                for (; e + G < e1; e += 2 * G) {
-                    const int i0 = ridx[e], i1 = ridx[e + G];
-                    const float s0 = __ldcg(Sr + c2r[e]), s1 = __ldcg(Sr + c2r[e + G]);
-                    float x0[RP], x1[RP];
-                    load_row_cg<RP>(Xn + (int64_t)(row0 + i0) * R, R, x0);
-                    load_row_cg<RP>(Xn + (int64_t)(row0 + i1) * R, R, x1);
+            for (int c = 0; c < RP; ++c) acc[c] = 0.f;
+            const int e1 = cp[j + 1];
+            const float* Xs = Xn + (int64_t)row0 * R;
+            for (int e0 = cp[j] + lane; e0 < e1; e0 += kAdmBatch * G) {
+                int ii[kAdmBatch];
+                float sv[kAdmBatch];
 #pragma unroll
-                    for (int c = 0; c < RP; ++c) acc[c] = fmaf(s1, x1[c], fmaf(s0, x0[c], acc[c]));
+                for (int u = 0; u < kAdmBatch; ++u) {
+                    const int e = e0 + u * G;
+                    ii[u] = e < e1 ? ridx[e] : -1;
+                    sv[u] = e < e1 ? Sr[e] : 0.f;
                 }
-                if (e < e1) {
-                    const float s0 = __ldcg(Sr + c2r[e]);
-                    float x0[RP];
-                    load_row_cg<RP>(Xn + (int64_t)(row0 + ridx[e]) * R, R, x0);
 #pragma unroll
-                    for (int c = 0; c < RP; ++c) acc[c] = fmaf(s0, x0[c], acc[c]);
-                }
-                // the lane that owns component c adds beta v_c - pi_c
+                for (int u = 0; u < kAdmBatch; ++u) {
+                    if (ii[u] < 0) break;
+                    float x[RP];
+                    load_f<RP>(staged_x, sY, Xs, ii[u], R, x);
 #pragma unroll
-                for (int c = 0; c < RP; ++c)
-                    if (c < R && (c & (G - 1)) == lane)
-                        acc[c] += fmaf(beta, __ldcg(Vb + col + c), -__ldcg(Pb + col + c));
-                group_reduce<RP>(acc, G, gmask);
-                for (int c = lane; c < R; c += G) {
-                    float v = 0.f;
-#pragma unroll
-                    for (int q = 0; q < RP; ++q) v = fmaf(sD[c * RP + q], yo[q], v);
-#pragma unroll
-                    for (int q = 0; q < RP; ++q) v = fmaf(sInv[c * RP + q], acc[q], v);
-                    const float pi = __ldcg(Pb + col + c);
-                    const float vv = fmaxf(0.f, v + pi / beta);
-                    Yb[col + c] = v;
-                    Vb[col + c] = vv;
-                    Pb[col + c] = pi + gamma * beta * (v - vv);
+                    for (int c = 0; c < RP; ++c) acc[c] = fmaf(sv[u], x[c], acc[c]);
                 }
             }
-            __syncthreads();
+            if (lane == 0) {  // beta V_k - Pi_k, once per column
+                float v[RP], pv[RP];
+                load_row_cg<RP>(Vb + col, R, v);
+                load_row_cg<RP>(Pb + col, R, pv);
+#pragma unroll
+                for (int c = 0; c < RP; ++c) acc[c] += fmaf(beta, v[c], -pv[c]);
+            }
+            group_reduce<RP>(acc, G, gmask);
+            for (int c = lane; c < R; c += G) {
+                float v = 0.f;
+#pragma unroll
+                for (int q2 = 0; q2 < RP; ++q2) v = fmaf(sD[c * RP + q2], yo[q2], v);
+#pragma unroll
+                for (int q2 = 0; q2 < RP; ++q2) v = fmaf(sInv[c * RP + q2], acc[q2], v);
+                const float pi = __ldcg(Pb + col + c);
+                const float vv = fmaxf(0.f, v + pi / beta);
+                Yb[col + c] = v;
+                Vb[col + c] = vv;
+                Pb[col + c] = pi + gamma * beta * (v - vv);
+            }
+        }
+        __syncthreads();
+        {
 #pragma unroll
             for (int q = 0; q < NE; ++q) gA[q] = 0.f;
-            gram_rows<RP, NE>(Yb + (int64_t)clo * R, nullptr, chi - clo, R, sY, gA, gA);
+            auto line = [&](int l) { return ordc[sched_pos(shc, l, k, K)]; };
+            gram_rows<RP, NE>(Yb, nullptr, shc.lines, R, line, sY, gA, gA);
             store_part<RP, NE>(sPartA, gA);
         }
         __threadfence();
@@ -478,11 +599,7 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
             cluster_sum(cl, K, sPartA, sM, RP * RP);
             __syncthreads();
             if (tid < 32) gj_inverse<RP>(sM, alpha, sInv, tid);
-            if (staged)
-                for (int e = tid; e < ns * RP; e += kAdmThreads) {
-                    const int j = e / RP, c = e % RP;
-                    sY[e] = c < R ? __ldcg(Yb + (int64_t)j * R + c) : 0.f;
-                }
+            if (staged) stage_rows<RP>(sY, Yb, ns, R);
             __syncthreads();
         }
     }
@@ -498,7 +615,7 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
 template <int RP>
 lt_status launch_adm(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const Omega& om, const AdmArgs& a,
                      SeedRef sr) {
-    const size_t dyn = (size_t)std::max(2 * kAdmChunk, a.stage_cols) * RP * 4;
+    const size_t dyn = (size_t)std::max(2 * kAdmChunk, a.stage_cap) * RP * 4;
     LT_CUDA(ctx, cudaFuncSetAttribute(k_adm<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     // the largest cluster (8, 4 or 2 CTAs) with which all slices fit at two CTAs per SM
     int K = kAdmMaxK;
@@ -543,7 +660,10 @@ extern "C" lt_status lt_complete_adm(lt_ctx* ctx, const lt_frame* f, const lt_sa
     if (st != LT_OK) return st;
     const size_t nx = (size_t)f->m * R, ny = (size_t)S * C * R;
     auto up = [](size_t n) { return (n * 4 + 255) & ~(size_t)255; };
-    char* p = (char*)lt_scratch(ctx, SCR_ADM, 3 * up(nx) + 2 * up(ny) + up((size_t)E), &st);
+    char* p = (char*)lt_scratch(ctx, SCR_ADM,
+                                3 * up(nx) + 2 * up(ny) + up((size_t)E) + up((size_t)f->m) + up((size_t)S * C) +
+                                    up((size_t)S * 16),
+                                &st);
     if (!p) return st;
     AdmArgs a;
     a.X0 = uv->U;
@@ -554,13 +674,21 @@ extern "C" lt_status lt_complete_adm(lt_ctx* ctx, const lt_frame* f, const lt_sa
     a.Vp = (float*)(p + 3 * up(nx));
     a.Pi = (float*)(p + 3 * up(nx) + up(ny));
     a.S = (float*)(p + 3 * up(nx) + 2 * up(ny));
+    int32_t* ordr = (int32_t*)(p + 3 * up(nx) + 2 * up(ny) + up((size_t)E));
+    int32_t* ordc = (int32_t*)((char*)ordr + up((size_t)f->m));
+    int32_t* ncls = (int32_t*)((char*)ordc + up((size_t)S * C));
+    a.ordr = ordr;
+    a.ordc = ordc;
+    a.ncls = ncls;
+    k_adm_order<<<dim3(S, 2), 1024, 0, ctx->stream>>>(*f, *smp, om, ordr, ordc, ncls);
+    LT_LAUNCH_CHECK(ctx, "k_adm_order");
     a.R = R;
     a.rk = uv->rank;
     a.iters = iters;
     a.alpha_rel = alpha_rel;
     a.gamma = gamma;
     const int RP = R <= 8 ? 8 : R <= 16 ? 16 : 32;
-    a.stage_cols = (int)std::min<size_t>((size_t)C, kAdmStageBytes / ((size_t)RP * 4));
+    a.stage_cap = (int)(kAdmStageBytes / ((size_t)RP * 4));
     const SeedRef sr = seed_ref(ctx, seed);
     if (RP == 8) return launch_adm<8>(ctx, f, smp, om, a, sr);
     if (RP == 16) return launch_adm<16>(ctx, f, smp, om, a, sr);

@@ -335,7 +335,7 @@ __global__ void k_om_scatter(lt_frame F, lt_samples smp, Omega om) {
             om.cval[o + rp[r] + kr] = v;
             om.ridx[o + cp[c] + kc] = (uint16_t)r;
             om.rval[o + cp[c] + kc] = v;
-            om.c2r[o + cp[c] + kc] = rp[r] + kr;
+            om.r2c[o + rp[r] + kr] = cp[c] + kc;
         }
         if (om.sell) {
             const int64_t pr = sell_slot(om.rcls + (int64_t)s * 16, om.rtb + (int64_t)s * om.tcap,
@@ -1155,7 +1155,7 @@ lt_status omega_build(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int
     om.cval = (float*)take(e_csr * 4);
     om.ridx = (uint16_t*)take(e_csr * 2);
     om.rval = (float*)take(e_csr * 4);
-    om.c2r = (int32_t*)take(e_csr * 4);
+    om.r2c = (int32_t*)take(e_csr * 4);
     om.mu = (float*)take(S * 4);
     om.bm = (uint32_t*)take((size_t)S * om.bm_stride * 4);
     om.bt = (uint32_t*)take((size_t)S * om.bt_stride * 4);

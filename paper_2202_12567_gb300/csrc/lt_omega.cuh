@@ -24,7 +24,7 @@ struct Omega {
     float* cval;        // [off[S]]
     uint16_t* ridx;     // [off[S]]     CSC row of each entry
     float* rval;        // [off[S]]
-    int32_t* c2r;       // [off[S]]     CSR slot (within the slice) of each CSC entry
+    int32_t* r2c;       // [off[S]]     CSC slot (within the slice) of each CSR entry
     float* mu;          // [S] mean observed value
     uint32_t* bm;       // row-major bitmaps
     uint32_t* bt;       // column-major bitmaps
