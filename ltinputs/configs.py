@@ -76,3 +76,9 @@ CONFIGS["room256_vpl16k_2box"] = dict(
     glossy_frac=0.0, n_slices=64, rate=0.15, rate1=0.002, rank=16, als_iters=10,
     max_cut=16384, tau=0.0005, d_min=0.1, scene_seed=5000,
 )
+
+# 256x256 points, 16384 VPLs, two boxes, colour: RGB face albedos and a warm light
+# (the paper's coloured scenes); the three channels are stacked as rows of a slice.
+CONFIGS["room256_vpl16k_2box_rgb"] = dict(
+    CONFIGS["room256_vpl16k_2box"], rgb=True, light_rgb=(1.0, 0.85, 0.7),
+)

@@ -21,6 +21,12 @@ Array layouts (float32, "three float4 planes"):
   vpls  [3, n, 4]: [px py pz albedo] [nx ny nz gloss] [ix iy iz flux] (i = unit dir to light)
   boxes [nb, 6]  : [xmin ymin zmin xmax ymax zmax]
 
+Colour (cfg["rgb"] true): every face also draws an RGB albedo from U[0.2, 0.8]^3 (a
+separate seeded stream, so the geometry and the VPLs stay those of the grey scene)
+and the light has colour cfg["light_rgb"]; the scalar albedo and flux then become
+the Rec. 709 luminances of the colours, and ``Scene.rgb`` holds point_albedo [m, 3],
+vpl_albedo [n, 3] and vpl_flux [n, 3] (float32).
+
 Everything here is input generation: the nearest-hit ray caster below only places
 points and lights.  It uses numpy's PCG64 generator seeded per scene.
 """
@@ -32,6 +38,7 @@ import math
 import numpy as np
 
 CAMERA_POS = np.array([0.5, 0.5, -1.35])
+LUMINANCE = np.array([0.2126, 0.7152, 0.0722])  # Rec. 709 weights of R, G, B
 CAMERA_VFOV_DEG = 40.0
 
 # wall ids 0..4: floor, ceiling, x=0, x=1, back
@@ -47,6 +54,7 @@ class Scene:
     width: int
     height: int
     n_emitted: int
+    rgb: dict | None = None    # colour arrays of an RGB scene (see the module notes)
 
     @property
     def m(self) -> int:
@@ -178,6 +186,11 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
     boxes = _make_boxes(cfg, rng)
     nb = boxes.shape[0]
     albedo, gloss = _materials(5 + 6 * nb, float(cfg.get("glossy_frac", 0.0)), rng)
+    colour = bool(cfg.get("rgb", False))
+    if colour:
+        face_rgb = np.random.default_rng(seed + 7919).uniform(0.2, 0.8, size=(5 + 6 * nb, 3))
+        albedo = face_rgb @ LUMINANCE
+        light_rgb = np.asarray(cfg.get("light_rgb", (1.0, 0.85, 0.7)), dtype=np.float64)
 
     # shading points
     width, height = int(cfg["width"]), int(cfg["height"])
@@ -235,8 +248,14 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
     vpls[1, :, 3] = gloss[vface]
     vpls[2, :, :3] = vdir
     vpls[2, :, 3] = power / n_emitted
+    rgb = None
+    if colour:
+        vpls[2, :, 3] = power / n_emitted * float(light_rgb @ LUMINANCE)
+        rgb = dict(point_albedo=face_rgb[face].astype(np.float32),
+                   vpl_albedo=face_rgb[vface].astype(np.float32),
+                   vpl_flux=np.broadcast_to(power / n_emitted * light_rgb, (n, 3)).astype(np.float32))
     return Scene(cfg=cfg, boxes=boxes, points=points, vpls=vpls, width=width, height=height,
-                 n_emitted=int(n_emitted))
+                 n_emitted=int(n_emitted), rgb=rgb)
 
 
 def single_quad_scene(vpl_pos, vpl_nrm, vpl_flux, vpl_albedo, quad_y: float, res: int,
