@@ -242,6 +242,38 @@ lt_status lt_slice_ranks(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, 
 lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
                     const float* w, const int32_t* row_perm, float* img);
 
+/* ---- Colour: three channels stacked as rows of a slice --------------------
+ * The paper renders coloured scenes (Sec. 6) and prints only the scalar matrix.
+ * Channel k of an entry takes each factor's colour in channel k: the point's albedo
+ * rho_p,k and the node intensity I_c,k = sum of the node's VPL powers
+ * Phi_k rho_q,k.  An entry of the scalar frame factors as A(i, c) = rho_p(i) I_c
+ * K(i, rep(c)) (K: geometry, BRDF shape, visibility; rho_p the frame's scalar
+ * albedo, I_c the tree's intensity), so A_k(i, c) = A(i, c) (rho_p,k / rho_p)
+ * (I_c,k / I_c): sampling runs on the scalar frame and every sampled pair gives
+ * the three channels without another shadow ray.  Slice s of m' pixels becomes a
+ * slice of 3m' rows, row 3i + k holding channel k of pixel i; lt_complete or
+ * lt_complete_adm and lt_render then run on the stacked frame (the frame with
+ * slice_off = slice_off3, m = 3m, max_rows = 3 max_rows) and write the image as
+ * [m][3] through row_perm3.  All arrays device, caller-allocated. */
+typedef struct {
+    float* pt_ratio;      /* [m][4] rho_p,k / rho_p of slice-ordered row r (k < 3; 0 where rho_p = 0) */
+    float* node_ratio;    /* [2n-1][4] I_v,k / I_v of tree node v (0 where I_v = 0) */
+    int32_t* slice_off3;  /* [S+1] 3 slice_off */
+    int32_t* row_perm3;   /* [3m] stacked row 3r + k -> image element 3 row_perm[r] + k */
+} lt_rgb;
+/* Fills `out` from pt_albedo [m][4] (RGB albedo of each pixel, image order) and
+ * vpl_power [n][4] (Phi_k rho_q,k of each VPL).  LT_EINVAL when 3 max_rows > 65535
+ * (stacked rows must fit the 16-bit row of a key). */
+lt_status lt_rgb_setup(lt_ctx* ctx, const lt_frame* f, const float* pt_albedo, const float* vpl_power,
+                       const int32_t* row_perm, lt_rgb* out);
+/* Entry e of slice s (key (i, c), value v) -> entries 3e + k of the stacked slice:
+ * key (3i + k, c), value v pt_ratio[row][k] node_ratio[col_node][k]; sets cnt = 3
+ * cnt, n1 = 3 n1 and ncol of smp3.  smp3->off is the stacked capacity layout (3 off
+ * of smp suffices); a slice beyond its capacity latches LT_ELIMIT and keeps the
+ * entries that fit. */
+lt_status lt_expand_rgb(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_rgb* c,
+                        lt_samples* smp3);
+
 /* ---- Launch tuning (no counterpart in the paper) ---------------------------
  * Launch shapes the library lets a caller tune per workload; they change no result
  * beyond the float summation order of the ALS Gram (als_lane_entries).  The values

@@ -55,6 +55,10 @@ class lt_factors(ctypes.Structure):
     _fields_ = [("r", _i32), ("U", _p), ("V", _p), ("rank", _p)]
 
 
+class lt_rgb(ctypes.Structure):
+    _fields_ = [("pt_ratio", _p), ("node_ratio", _p), ("slice_off3", _p), ("row_perm3", _p)]
+
+
 class lt_params(ctypes.Structure):
     _fields_ = [("rate1", _f32), ("tau", _f32), ("d_min", _f32), ("rate", _f32), ("als_iters", _i32),
                 ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32), ("rank_cols", _i32),
@@ -99,6 +103,9 @@ _SIGS = {
                            ctypes.POINTER(lt_factors)]),
     "lt_complete_adm": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _f32, _u64,
                                ctypes.POINTER(lt_factors)]),
+    "lt_rgb_setup": (_i32, [_p, ctypes.POINTER(lt_frame), _p, _p, _p, ctypes.POINTER(lt_rgb)]),
+    "lt_expand_rgb": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_rgb),
+                             ctypes.POINTER(lt_samples)]),
     "lt_render": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors), _p,
                          _p, _p]),
     "lt_render_frame": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_params), _u64,
@@ -358,6 +365,61 @@ class Samples:
             self.col_node[s * C:s * C + n].cpu().numpy(), self.g[s * C:s * C + n].cpu().numpy()
 
 
+class RGB:
+    """Colour tables of a frame (lt_rgb) and the stacked frame, samples, factors and
+    image: slice s of m' pixels becomes 3m' rows, row 3i + k = channel k of pixel i."""
+
+    def __init__(self, frame: Frame, smp: Samples, r: int, per_slice: bool = False):
+        dev = frame.pts_s.device
+        n = frame.vpls.shape[1]
+        self.pt_ratio = torch.zeros(frame.m * 4, dtype=torch.float32, device=dev)
+        self.node_ratio = torch.zeros((2 * n - 1) * 4, dtype=torch.float32, device=dev)
+        self.slice_off3 = torch.zeros(frame.S + 1, dtype=torch.int32, device=dev)
+        self.row_perm3 = torch.zeros(3 * frame.m, dtype=torch.int32, device=dev)
+        self._s = lt_rgb(_ptr(self.pt_ratio), _ptr(self.node_ratio), _ptr(self.slice_off3), _ptr(self.row_perm3))
+        f = frame.struct()
+        self._f3 = lt_frame(f.pts, 3 * frame.m, f.vpls, f.n, _ptr(self.slice_off3), f.S, 3 * f.max_rows, f.tree,
+                            f.C, f.forest, f.level_off, f.level_nodes, f.H)
+        # stacked samples: three times the capacity of every slice
+        i32 = dict(dtype=torch.int32, device=dev)
+        self.off_host = 3 * smp.off_host
+        self.off = torch.from_numpy(self.off_host).to(dev)
+        self.key = torch.zeros(int(self.off_host[-1]), **i32)
+        self.val = torch.zeros(int(self.off_host[-1]), dtype=torch.float32, device=dev)
+        self.ncol = torch.zeros(frame.S, **i32)
+        self.n1 = torch.zeros(frame.S, **i32)
+        self.cnt = torch.zeros(frame.S, **i32)
+        self.col_node, self.g = smp.col_node, smp.g
+        self._smp3 = lt_samples(_ptr(self.ncol), _ptr(smp.col_node), _ptr(smp.g), _ptr(self.off), _ptr(self.key),
+                                _ptr(self.val), _ptr(self.n1), _ptr(self.cnt))
+        self.r = r
+        self.U = torch.zeros(3 * frame.m * r, dtype=torch.float32, device=dev)
+        self.V = torch.zeros(frame.S * frame.C * r, dtype=torch.float32, device=dev)
+        self.rank = torch.full((frame.S,), r, dtype=torch.int32, device=dev) if per_slice else None
+        self._uv3 = lt_factors(r, _ptr(self.U), _ptr(self.V), _ptr(self.rank))
+        self.img = torch.zeros(3 * frame.m, dtype=torch.float32, device=dev)
+        self.C = frame.C
+
+    def struct(self) -> lt_rgb:
+        return self._s
+
+    def frame3(self) -> lt_frame:
+        return self._f3
+
+    def samples3(self) -> lt_samples:
+        return self._smp3
+
+    def factors3(self) -> lt_factors:
+        return self._uv3
+
+    def slice(self, s: int):
+        """Host copies (rows, cols, vals) of stacked slice s."""
+        o = int(self.off_host[s])
+        c = int(self.cnt[s].item())
+        key = self.key[o:o + c].cpu().numpy().astype(np.uint32)
+        return (key >> 16).astype(np.int64), (key & 0xFFFF).astype(np.int64), self.val[o:o + c].cpu().numpy()
+
+
 class Factors:
     """U, V with row stride r; per_slice=True adds the per-slice rank array [S]."""
 
@@ -410,6 +472,35 @@ def lt_complete_adm(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters
     ctx._check("lt_complete_adm", ctx.lib.lt_complete_adm(ctx.h, ctypes.byref(frame.struct()),
                                                           ctypes.byref(smp.struct()), iters, alpha_rel, gamma, seed,
                                                           ctypes.byref(uv.struct())))
+
+
+def lt_rgb_setup(ctx: Context, frame: Frame, rgb: RGB, pt_albedo, vpl_power, row_perm):
+    """pt_albedo [m, 4] (image order) and vpl_power [n, 4] device float32 tensors."""
+    ctx._check("lt_rgb_setup", ctx.lib.lt_rgb_setup(ctx.h, ctypes.byref(frame.struct()), _ptr(pt_albedo),
+                                                    _ptr(vpl_power), _ptr(row_perm), ctypes.byref(rgb.struct())))
+
+
+def lt_expand_rgb(ctx: Context, frame: Frame, smp: Samples, rgb: RGB):
+    ctx._check("lt_expand_rgb", ctx.lib.lt_expand_rgb(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
+                                                      ctypes.byref(rgb.struct()), ctypes.byref(rgb.samples3())))
+
+
+def lt_complete_rgb(ctx: Context, rgb: RGB, iters, lam_rel, seed, adm=None):
+    """Completion of the stacked slices: lt_complete, or lt_complete_adm when adm =
+    (iters, alpha_rel, gamma)."""
+    f3, s3, uv3 = rgb.frame3(), rgb.samples3(), rgb.factors3()
+    if adm is None:
+        ctx._check("lt_complete", ctx.lib.lt_complete(ctx.h, ctypes.byref(f3), ctypes.byref(s3), iters, lam_rel, seed,
+                                                      ctypes.byref(uv3)))
+    else:
+        ctx._check("lt_complete_adm", ctx.lib.lt_complete_adm(ctx.h, ctypes.byref(f3), ctypes.byref(s3), adm[0],
+                                                              adm[1], adm[2], seed, ctypes.byref(uv3)))
+
+
+def lt_render_rgb(ctx: Context, rgb: RGB):
+    """The stacked image into rgb.img ([m][3], image order)."""
+    ctx._check("lt_render", ctx.lib.lt_render(ctx.h, ctypes.byref(rgb.frame3()), ctypes.byref(rgb.samples3()),
+                                              ctypes.byref(rgb.factors3()), None, _ptr(rgb.row_perm3), _ptr(rgb.img)))
 
 
 def lt_render(ctx: Context, frame: Frame, smp: Samples, uv: Factors, row_perm, img, w=None):

@@ -127,6 +127,53 @@ class Renderer:
             lt.lt_sync(self.ctx)
         return self.img
 
+    # ---------------------------------------------------------------- colour
+    def setup_rgb(self):
+        """Colour tables and the stacked frame of an RGB scene (scene.rgb)."""
+        rgb = self.scene.rgb
+        m, n = self.scene.m, self.scene.n
+        pa = np.zeros((m, 4), dtype=np.float32)
+        pa[:, :3] = rgb["point_albedo"]
+        vp = np.zeros((n, 4), dtype=np.float32)
+        vp[:, :3] = rgb["vpl_flux"].astype(np.float64) * rgb["vpl_albedo"]
+        self.rgb = lt.RGB(self.frame, self.smp, self.cfg["rank"], per_slice=int(self.cfg.get("rank_cols", 0)) > 0)
+        self._rgb_in = (torch.from_numpy(pa).to(self.dev), torch.from_numpy(vp).to(self.dev))
+        lt.lt_rgb_setup(self.ctx, self.frame, self.rgb, self._rgb_in[0], self._rgb_in[1], self.row_perm)
+        return self
+
+    def render_rgb(self, seed=None, weights=None, sync=True):
+        """One colour frame: scalar sampling and evaluation, the three channels of every
+        sample, completion of the stacked slices, image [m][3]."""
+        c = self.cfg
+        seed = c["frame_seed"] if seed is None else seed
+        self.pass1(seed)
+        self.pass2(seed, weights)
+        self.evaluate()
+        lt.lt_expand_rgb(self.ctx, self.frame, self.smp, self.rgb)
+        if self.rgb.rank is not None:
+            lt.lt_slice_ranks(self.ctx, self.frame, self.smp, c["rank"], c["rank_cols"], self.rgb.rank)
+        adm = (c["adm_iters"], c["adm_alpha_rel"], c["adm_gamma"]) if c.get("completion", "als") == "adm" else None
+        lt.lt_complete_rgb(self.ctx, self.rgb, c["als_iters"], c["lam_rel"], seed, adm)
+        lt.lt_render_rgb(self.ctx, self.rgb)
+        if sync:
+            lt.lt_sync(self.ctx)
+        return self.rgb.img.view(-1, 3)
+
+    def bruteforce_rgb(self):
+        """The full image over all VPLs per channel [m][3] (k_bruteforce per channel)."""
+        rgb = self.scene.rgb
+        out = torch.zeros((self.scene.m, 3), dtype=torch.float32, device=self.dev)
+        for k in range(3):
+            pts = self.pts.clone()
+            pts[0, :, 3] = torch.from_numpy(np.ascontiguousarray(rgb["point_albedo"][:, k])).to(self.dev)
+            vpl = self.vpls.clone()
+            vpl[0, :, 3] = torch.from_numpy(np.ascontiguousarray(rgb["vpl_albedo"][:, k])).to(self.dev)
+            vpl[2, :, 3] = torch.from_numpy(np.ascontiguousarray(rgb["vpl_flux"][:, k])).to(self.dev)
+            img = torch.empty(self.scene.m, dtype=torch.float32, device=self.dev)
+            lt.lt_bruteforce(self.ctx, pts, vpl, self.cfg["d_min"], img)
+            out[:, k] = img
+        return out
+
     def bruteforce(self, out=None):
         return lt.lt_bruteforce(self.ctx, self.pts, self.vpls, self.cfg["d_min"], out)
 
