@@ -170,6 +170,18 @@ lt_status lt_cut_forest(lt_ctx* ctx, const lt_tree* tree, const int32_t* cut, in
  * inside a slice), slice_off[S+1] delimits the slices. */
 lt_status lt_make_slices(lt_ctx* ctx, const float* pts, int64_t m, int32_t S, int32_t iters,
                          float normal_weight, int32_t* row_perm, int32_t* slice_off);
+/* The paper's own slicing (Sec. 6 step 2; slices of about `target` pixels, Sec. 3):
+ * the 6-D vectors (p, w n) are split recursively into a binary tree.  A node of
+ * n > target points splits along the feature dimension of largest extent (float32
+ * extents, the first largest) at the median: the floor(n/2) points smallest in
+ * (feature value, pixel index) go left keeping their order, the rest go right.
+ * Leaves left to right are the slices (pixels ascending inside a slice).  The slice
+ * sizes depend on m and target only: lt_split_slice_count gives their number S (a
+ * host computation; -1 for bad arguments), slice_off[S+1] is written from them.
+ * Synchronous (the level layout is copied from host memory). */
+int32_t lt_split_slice_count(int64_t m, int32_t target);
+lt_status lt_make_slices_split(lt_ctx* ctx, const float* pts, int64_t m, int32_t target, float normal_weight,
+                               int32_t* row_perm, int32_t* slice_off);
 /* pts_out[3][m][4] = pts with rows permuted by row_perm. */
 lt_status lt_permute_points(lt_ctx* ctx, const float* pts, int64_t m, const int32_t* row_perm,
                             float* pts_out);

@@ -18,10 +18,14 @@ import copy
 #   rank      completion rank r (the paper's q, Sec. 5)
 #   als_iters fixed number of alternating least-squares sweeps
 #   lam_rel   ridge term relative to the mean Gram diagonal
+#   slicing   "kmeans" (n_slices clusters) or "split6d" (the paper's recursive 6-D
+#             binary split into slices of at most slice_size pixels)
 #   completion  "als" (masked ALS) or "adm" (the nonnegative ADM of App. A) with
 #             adm_iters iterations, penalties adm_alpha_rel times the start's mean
 #             Gram diagonal, and step gamma adm_gamma
 _BASE = dict(
+    slicing="kmeans",
+    slice_size=800,
     completion="als",
     adm_iters=100,
     adm_alpha_rel=0.3,

@@ -43,7 +43,10 @@ def setup(scene, cfg, cut=None, slicing=None):
         cut = cut_mod.build_global_cut(tree, scene.points, scene.vpls, scene.width, scene.height,
                                        eps=cfg["eps_cut"], max_cut=cfg["max_cut"], d_min=cfg["d_min"])
     forest = pass1.build_forest(tree, cut)
-    if slicing is None:
+    if slicing is None and cfg.get("slicing", "kmeans") == "split6d":
+        row_perm, slice_off = slices_mod.split6d_slices(scene.points, cfg["slice_size"],
+                                                        cfg["slice_feature_normal_weight"])
+    elif slicing is None:
         row_perm, slice_off, _, _ = slices_mod.kmeans_slices(
             scene.points, cfg["n_slices"], cfg["kmeans_iters"], cfg["slice_feature_normal_weight"])
     else:

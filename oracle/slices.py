@@ -1,9 +1,9 @@
 """Matrix slicing: cluster the shading points by position and normal (Sec. 3 step 2).
 
 The paper partitions the rows of A by clustering the 6-D (coordinate, normal)
-vectors of the surface points, following the lightslice method (and implements it
-as a recursive binary split on the GPU, Sec. 6).  The reading taken here is Lloyd's
-k-means into S slices:
+vectors of the surface points, following the lightslice method, and implements it
+as a recursive binary split on the GPU (Sec. 6; ``split6d_slices`` below).  The
+default reading taken here is Lloyd's k-means into S slices:
 
 * feature of point i: (p_x, p_y, p_z, w n_x, w n_y, w n_z), w = 0.3;
 * initial centroids: the points of rank floor((k + 1/2) m / S), k = 0..S-1, in the
@@ -56,6 +56,46 @@ def kmeans_slices(points, n_slices: int, iters: int = 10, w: float = 0.3):
     counts = np.bincount(lab, minlength=S)
     slice_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     return row_perm.astype(np.int64), slice_off, lab, C
+
+
+def split_sizes(m: int, target: int) -> list[int]:
+    """Slice sizes of the recursive binary split, left to right: a node of n > target
+    points splits into floor(n/2) (left) and the rest; depends on m and target only."""
+    if m <= target:
+        return [m]
+    return split_sizes(m // 2, target) + split_sizes(m - m // 2, target)
+
+
+def split6d_slices(points, target: int, w: float = 0.3):
+    """The paper's own slicing (Sec. 6 step 2; slices of about `target` pixels, Sec. 3):
+    the 6-D vectors (p, w n) are split recursively into a binary tree.  Reading: a
+    node with more than `target` points splits along the feature dimension of largest
+    extent (float32 extents, first largest), at the median: the floor(n/2) points
+    smallest in (feature value, pixel index) go left, keeping their order, the rest go
+    right.  Returns (row_perm [m], slice_off [S+1]) with the leaves left to right;
+    inside a slice the pixels stay in ascending order."""
+    P = np.asarray(points, dtype=np.float32)
+    X = np.concatenate([P[0, :, :3], np.float32(w) * P[1, :, :3]], axis=1).astype(np.float32)
+    m = X.shape[0]
+    out = []
+
+    def split(idx):
+        n = idx.size
+        if n <= target:
+            out.append(idx)
+            return
+        ext = X[idx].max(axis=0) - X[idx].min(axis=0)
+        d = int(np.argmax(ext))
+        order = np.lexsort((idx, X[idx, d]))  # by value, then pixel index
+        left = np.zeros(n, dtype=bool)
+        left[order[:n // 2]] = True
+        split(idx[left])
+        split(idx[~left])
+
+    split(np.arange(m, dtype=np.int64))
+    row_perm = np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
+    slice_off = np.concatenate([[0], np.cumsum([a.size for a in out])]).astype(np.int64)
+    return row_perm, slice_off
 
 
 def permute_points(points, row_perm) -> np.ndarray:

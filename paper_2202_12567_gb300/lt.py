@@ -103,6 +103,8 @@ _SIGS = {
                            ctypes.POINTER(lt_factors)]),
     "lt_complete_adm": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _f32, _u64,
                                ctypes.POINTER(lt_factors)]),
+    "lt_split_slice_count": (_i32, [_i64, _i32]),
+    "lt_make_slices_split": (_i32, [_p, _p, _i64, _i32, _f32, _p, _p]),
     "lt_rgb_setup": (_i32, [_p, ctypes.POINTER(lt_frame), _p, _p, _p, ctypes.POINTER(lt_rgb)]),
     "lt_expand_rgb": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_rgb),
                              ctypes.POINTER(lt_samples)]),
@@ -472,6 +474,21 @@ def lt_complete_adm(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters
     ctx._check("lt_complete_adm", ctx.lib.lt_complete_adm(ctx.h, ctypes.byref(frame.struct()),
                                                           ctypes.byref(smp.struct()), iters, alpha_rel, gamma, seed,
                                                           ctypes.byref(uv.struct())))
+
+
+def lt_make_slices_split(ctx: Context, pts, target: int, normal_weight: float):
+    """Recursive 6-D binary split into slices of at most `target` points; returns
+    (row_perm [m], slice_off [S+1]) device int32 tensors."""
+    m = pts.shape[1]
+    S = int(ctx.lib.lt_split_slice_count(m, int(target)))
+    if S < 1:
+        raise RuntimeError("lt_split_slice_count: bad arguments")
+    row_perm = torch.empty(m, dtype=torch.int32, device=pts.device)
+    slice_off = torch.empty(S + 1, dtype=torch.int32, device=pts.device)
+    ctx._check("lt_make_slices_split", ctx.lib.lt_make_slices_split(ctx.h, _ptr(pts), m, int(target),
+                                                                    float(normal_weight), _ptr(row_perm),
+                                                                    _ptr(slice_off)))
+    return row_perm, slice_off
 
 
 def lt_rgb_setup(ctx: Context, frame: Frame, rgb: RGB, pt_albedo, vpl_power, row_perm):

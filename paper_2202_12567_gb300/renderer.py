@@ -52,7 +52,10 @@ class Renderer:
             cut = torch.as_tensor(np.asarray(cut), dtype=torch.int32).to(self.dev)
         self.cut = cut
         forest, level_off, level_nodes, H = lt.lt_cut_forest(ctx, self.tree, cut)
-        if row_perm is None:
+        if row_perm is None and cfg.get("slicing", "kmeans") == "split6d":  # the paper's recursive split
+            row_perm, slice_off = lt.lt_make_slices_split(ctx, self.pts, cfg["slice_size"],
+                                                          cfg["slice_feature_normal_weight"])
+        elif row_perm is None:
             row_perm, slice_off = lt.lt_make_slices(ctx, self.pts, cfg["n_slices"], cfg["kmeans_iters"],
                                                     cfg["slice_feature_normal_weight"])
         else:

@@ -447,3 +447,50 @@ def test_rel_rmse_definition():
     ref = np.array([3.0, 4.0])
     assert bruteforce.rel_rmse(np.array([3.0, 4.0]), ref) == 0.0
     assert abs(bruteforce.rel_rmse(np.array([0.0, 0.0]), ref) - 1.0) < 1e-15
+
+
+# ---------------------------------------------------------------- 6-D recursive split slicing
+def _line_points(xs, normal=(0.0, 1.0, 0.0)):
+    P = np.zeros((3, len(xs), 4), dtype=np.float32)
+    P[0, :, 0] = xs
+    P[1, :, :3] = normal
+    return P
+
+
+def test_split_slices_of_points_on_a_line_are_runs_of_x():
+    rng = np.random.default_rng(3)
+    xs = rng.permutation(1000).astype(np.float32) / 1000
+    perm, off = slices_mod.split6d_slices(_line_points(xs), 100)
+    assert sorted(perm.tolist()) == list(range(1000))
+    assert np.diff(off).tolist() == slices_mod.split_sizes(1000, 100)
+    rank = np.argsort(np.argsort(xs))  # position of each pixel in x order
+    for s in range(len(off) - 1):
+        r = np.sort(rank[perm[off[s]:off[s + 1]]])
+        assert r[-1] - r[0] == r.size - 1  # a contiguous run of the x order
+        assert np.all(np.diff(perm[off[s]:off[s + 1]]) > 0)  # ascending pixels inside a slice
+    starts = [rank[perm[off[s]:off[s + 1]]].min() for s in range(len(off) - 1)]
+    assert starts == sorted(starts)  # left to right
+
+
+def test_split_sizes_and_ties():
+    assert slices_mod.split_sizes(1000, 100) == [62, 63, 62, 63, 62, 63, 62, 63, 62, 63, 62, 63, 62, 63, 62, 63]
+    assert slices_mod.split_sizes(50, 100) == [50]
+    assert slices_mod.split_sizes(7, 2) == [1, 2, 2, 2]
+    # identical features: the split falls back to the pixel index
+    perm, off = slices_mod.split6d_slices(_line_points(np.zeros(10, dtype=np.float32)), 3)
+    assert perm.tolist() == list(range(10)) and off.tolist() == [0, 2, 5, 7, 10]
+
+
+def test_split_takes_the_dimension_of_largest_extent():
+    # x spans 1, the normal's z spans 2 w = 0.6 < 1 < ... ; with w = 1 the normal wins
+    xs = np.linspace(0, 1, 8, dtype=np.float32)
+    P = _line_points(xs)
+    P[1, :, :3] = 0.0
+    P[1, :4, 2] = 1.0
+    P[1, 4:, 2] = -1.0
+    P[1, ::2, 2] *= -1.0  # normal z alternates against x
+    perm, off = slices_mod.split6d_slices(P, 4, w=0.3)
+    assert sorted(perm[:4].tolist()) == [0, 1, 2, 3]  # split on x
+    perm, off = slices_mod.split6d_slices(P, 4, w=1.0)
+    nz = P[1, :, 2]
+    assert np.all(nz[perm[:4]] < 0) and np.all(nz[perm[4:]] > 0)  # split on the normal
