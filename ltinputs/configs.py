@@ -14,6 +14,7 @@ import copy
 #   eps_cut   lightcuts relative error bound for the conservative global cut (Sec. 3 item 1)
 #   max_cut   cap on the global cut size (the paper's cuts hold ~800-900 nodes)
 #   tau       coarsening threshold relative to the slice's estimated mean pixel (Eq. 2)
+#   target_cut  > 0: coarsen each slice to this many nodes by cost order instead (Sec. 4)
 #   rate      sampling rate rho = |Omega_s| / (m'_s n'_s)  (Sec. 5)
 #   rank      completion rank r (the paper's q, Sec. 5)
 #   als_iters fixed number of alternating least-squares sweeps
@@ -24,6 +25,7 @@ import copy
 #             adm_iters iterations, penalties adm_alpha_rel times the start's mean
 #             Gram diagonal, and step gamma adm_gamma
 _BASE = dict(
+    target_cut=0,
     slicing="kmeans",
     slice_size=800,
     completion="als",

@@ -122,10 +122,32 @@ class Pass1Slice:
     n_rays: int
 
 
+def forest_heights(forest: Forest) -> np.ndarray:
+    """Height of every forest node (0 on the cut, 1 + the larger child height above)."""
+    nf = 2 * forest.C - 1
+    height = np.full(nf, -1, dtype=np.int64)
+    height[:forest.C] = 0
+    changed = True
+    while changed:
+        changed = False
+        for f in range(forest.C, nf):
+            a, b = forest.child[f]
+            if height[f] < 0 and height[a] >= 0 and height[b] >= 0:
+                height[f] = 1 + max(height[a], height[b])
+                changed = True
+    return height
+
+
 def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int, row0: int,
                   m_s: int, rate1: float, tau: float, seed: int, d_min=0.01,
-                  order_rng: np.random.Generator | None = None) -> Pass1Slice:
-    """Pass 1 + coarsening of slice s (rows row0 .. row0+m_s-1 of the slice-ordered points)."""
+                  order_rng: np.random.Generator | None = None, target: int | None = None) -> Pass1Slice:
+    """Pass 1 + coarsening of slice s (rows row0 .. row0+m_s-1 of the slice-ordered points).
+
+    With `target` the coarsening runs until the cut holds at most `target` nodes
+    instead of against tau (Sec. 4, last paragraph): the testable sibling pairs are
+    ordered by cost and merged from the least; a merge whose parent pair becomes
+    testable tests it and adds it to the order.  Ties of cost go to the pair of lower
+    forest height, then to the lower forest id (the paper leaves ties open)."""
     C = forest.C
     nf = 2 * C - 1
     if m_s == 0:
@@ -151,7 +173,7 @@ def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int
         rows[c] = draw_rows(seed, s, c, int(k[c]), m_s)
         vals[c] = entries(c, rows[c])
     s_hat = float(sum(v.mean() for v in (vals[c] for c in range(C)) if v.size))
-    thr = tau * s_hat
+    thr = tau * s_hat if target is None else float("inf")
 
     alive = np.zeros(nf, dtype=bool)
     alive[:C] = True
@@ -159,42 +181,73 @@ def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int
     cost = np.zeros(nf)
     rejected = {}
     log = []
-    while True:
-        ready = [f for f in range(C, nf)
-                 if not tested[f] and alive[forest.child[f, 0]] and alive[forest.child[f, 1]]]
-        if not ready:
-            break
-        if order_rng is not None:
-            order_rng.shuffle(ready)
-        for f in ready:
-            a, b = (int(x) for x in forest.child[f])
-            ta, tb = forest.node[a], forest.node[b]
-            p, q = (a, b) if tree.I[ta] >= tree.I[tb] else (b, a)
-            rf = np.union1d(rows[a], rows[b])
-            full = {}
-            for x in (a, b):
-                v = np.empty(rf.size)
-                have = np.isin(rf, rows[x])
-                v[have] = vals[x]           # rows[x] is sorted and a subset of rf
-                if np.any(~have):
-                    v[~have] = entries(x, rf[~have])
-                full[x] = v
-            Ip = float(tree.I[forest.node[p]])
-            Iq = float(tree.I[forest.node[q]])
-            If = float(tree.I[forest.node[f]])
-            eps = float(np.max(np.abs(full[q] - full[p] * (Iq / Ip)))) if rf.size else 0.0
-            cf = eps + cost[q]
-            merged = cf < thr
-            log.append((f, eps, cf, thr, bool(merged), p, q, rf, full[p], full[q]))
-            tested[f] = True
-            if merged:
-                alive[a] = alive[b] = False
-                alive[f] = True
-                rows[f] = rf
-                vals[f] = full[p] * (If / Ip)
-                cost[f] = cf
-            else:
-                rejected[f] = (rf, full[a], full[b])
+
+    def test_pair(f):
+        """Sec. 4 test of the pair under forest node f on zeta_f = zeta_a U zeta_b."""
+        a, b = (int(x) for x in forest.child[f])
+        ta, tb = forest.node[a], forest.node[b]
+        p, q = (a, b) if tree.I[ta] >= tree.I[tb] else (b, a)
+        rf = np.union1d(rows[a], rows[b])
+        full = {}
+        for x in (a, b):
+            v = np.empty(rf.size)
+            have = np.isin(rf, rows[x])
+            v[have] = vals[x]           # rows[x] is sorted and a subset of rf
+            if np.any(~have):
+                v[~have] = entries(x, rf[~have])
+            full[x] = v
+        Ip = float(tree.I[forest.node[p]])
+        Iq = float(tree.I[forest.node[q]])
+        eps = float(np.max(np.abs(full[q] - full[p] * (Iq / Ip)))) if rf.size else 0.0
+        tested[f] = True
+        return dict(f=f, a=a, b=b, p=p, q=q, rf=rf, full=full, eps=eps, cost=eps + cost[q])
+
+    def merge(t):
+        f, a, b, p = t["f"], t["a"], t["b"], t["p"]
+        alive[a] = alive[b] = False
+        alive[f] = True
+        rows[f] = t["rf"]
+        vals[f] = t["full"][p] * (float(tree.I[forest.node[f]]) / float(tree.I[forest.node[p]]))
+        cost[f] = t["cost"]
+
+    def ready(f):
+        return not tested[f] and alive[forest.child[f, 0]] and alive[forest.child[f, 1]]
+
+    if target is None:
+        while True:
+            todo = [f for f in range(C, nf) if ready(f)]
+            if not todo:
+                break
+            if order_rng is not None:
+                order_rng.shuffle(todo)
+            for f in todo:
+                t = test_pair(f)
+                merged = t["cost"] < thr
+                log.append((f, t["eps"], t["cost"], thr, bool(merged), t["p"], t["q"], t["rf"],
+                            t["full"][t["p"]], t["full"][t["q"]]))
+                if merged:
+                    merge(t)
+                else:
+                    rejected[f] = (t["rf"], t["full"][t["a"]], t["full"][t["b"]])
+    else:
+        height = forest_heights(forest)
+        cand = {}
+        for f in range(C, nf):
+            if ready(f):
+                cand[f] = test_pair(f)
+        n_live = C
+        while n_live > target and cand:
+            f = min(cand, key=lambda x: (cand[x]["cost"], height[x], x))
+            t = cand.pop(f)
+            log.append((f, t["eps"], t["cost"], thr, True, t["p"], t["q"], t["rf"], t["full"][t["p"]],
+                        t["full"][t["q"]]))
+            merge(t)
+            n_live -= 1
+            par = int(forest.parent[f])
+            if par >= 0 and ready(par):
+                cand[par] = test_pair(par)
+        for f, t in cand.items():  # tested and not merged
+            rejected[f] = (t["rf"], t["full"][t["a"]], t["full"][t["b"]])
 
     live = np.nonzero(alive)[0]
     live = live[np.argsort(tree.first[forest.node[live]], kind="stable")]

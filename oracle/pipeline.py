@@ -61,7 +61,7 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
     a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
     m_s = b - a
     p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.boxes, s, a, m_s, cfg["rate1"],
-                             cfg["tau"], seed, cfg["d_min"], order_rng)
+                             cfg["tau"], seed, cfg["d_min"], order_rng, target=target_cut(cfg))
     n_s = p1.col_node.size
     w = p1.g if weights is None else weights
     r2, c2, _, hit_cap = pass2.draw_pass2(seed, s, m_s, w, p1.rows * n_s + p1.cols, cfg["rate"])
@@ -80,6 +80,13 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
         res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["als_iters"],
                                           cfg["lam_rel"], seed, s)
     return res
+
+
+def target_cut(cfg):
+    """cfg["target_cut"] > 0: coarsen each slice to that many nodes by cost order
+    (Sec. 4); otherwise against tau."""
+    t = int(cfg.get("target_cut", 0))
+    return t if t > 0 else None
 
 
 def slice_rank(cfg, n_s: int) -> int:

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import adm, als, bruteforce, pass1, pass2, shading
+from . import adm, als, bruteforce, pass1, pass2, pipeline, shading
 
 
 def channel_vpls(vpls, rgb: dict, k: int):
@@ -118,7 +118,7 @@ def render_frame(scene, cfg, st, seed=None):
         a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
         m_s = b - a
         p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.boxes, s, a, m_s, cfg["rate1"], cfg["tau"],
-                                 seed, cfg["d_min"])
+                                 seed, cfg["d_min"], target=pipeline.target_cut(cfg))
         n_s = p1.col_node.size
         r2, c2, _, _ = pass2.draw_pass2(seed, s, m_s, p1.g, p1.rows * n_s + p1.cols, cfg["rate"])
         rows = np.concatenate([p1.rows, r2]).astype(np.int64)

@@ -494,3 +494,63 @@ def test_split_takes_the_dimension_of_largest_extent():
     perm, off = slices_mod.split6d_slices(P, 4, w=1.0)
     nz = P[1, :, 2]
     assert np.all(nz[perm[:4]] < 0) and np.all(nz[perm[4:]] > 0)  # split on the normal
+
+
+# ---------------------------------------------------------------- coarsening to a target cut size
+def _target_setup():
+    cfg = get_config("room64_vpl1k_2box")
+    sc = make_scene(cfg)
+    st = pipeline.setup(sc, cfg)
+    a, b = int(st["slice_off"][3]), int(st["slice_off"][4])
+    run = lambda **kw: pass1.coarsen_slice(st["tree"], st["forest"], st["pts_s"], sc.vpls, sc.boxes, 3, a, b - a,
+                                           cfg["rate1"], kw.pop("tau", cfg["tau"]), 7, cfg["d_min"], **kw)
+    return st, run
+
+
+def _same(x, y):
+    return (np.array_equal(x.col_node, y.col_node) and np.array_equal(x.rows, y.rows)
+            and np.array_equal(x.cols, y.cols) and np.array_equal(x.vals, y.vals) and np.array_equal(x.g, y.g))
+
+
+def test_target_limits_equal_the_threshold_limits():
+    st, run = _target_setup()
+    C = st["forest"].C
+    assert _same(run(target=C), run(tau=0.0))             # nothing merges
+    assert _same(run(target=1), run(tau=float("inf")))    # everything merges
+
+
+def test_target_sizes_are_met_and_nested():
+    st, run = _target_setup()
+    prev = None
+    for T in (600, 300, 100, 20):
+        r = run(target=T)
+        assert r.col_node.size == T
+        merged = {e[0] for e in r.log}
+        if prev is not None:
+            assert prev <= merged  # a smaller target merges a superset
+        prev = merged
+
+
+def test_target_order_is_the_effective_cost_order():
+    """Greedy by cost among testable pairs merges the K pairs of smallest effective cost
+    eff(f) = max(cost(f), eff(children)) (ties: lower height, lower id): the order the
+    GPU selects by."""
+    st, run = _target_setup()
+    forest = st["forest"]
+    C = forest.C
+    full = run(tau=float("inf"))
+    cost = {e[0]: e[2] for e in full.log}
+    height = pass1.forest_heights(forest)
+    eff = {}
+
+    def get(f):
+        if f < C:
+            return 0.0
+        if f not in eff:
+            eff[f] = max(cost[f], get(int(forest.child[f, 0])), get(int(forest.child[f, 1])))
+        return eff[f]
+
+    order = sorted(cost, key=lambda f: (get(f), height[f], f))
+    for T in (700, 400, 150, 30):
+        r = run(target=T)
+        assert {e[0] for e in r.log} == set(order[:C - T])
