@@ -196,6 +196,16 @@ lt_status lt_permute_points(lt_ctx* ctx, const float* pts, int64_t m, const int3
  * LT_ELIMIT. */
 lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, float d_min,
                           uint64_t seed, lt_samples* smp);
+/* Pass 1 with coarsening to a target cut size instead of tau (Sec. 4, the variant
+ * that orders the sibling pairs by cost and merges from the least): each slice ends
+ * with min(target, C) columns when its forest allows it (a forest of several trees
+ * stops at its roots).  Every sibling pair is tested (so every internal forest node
+ * has its cost); the merged pairs are the C - target of smallest effective cost
+ * max(cost, effective cost of the children), ties to the lower forest height and
+ * then the lower forest id, which is what merging the least-cost testable pair one
+ * at a time gives.  Outputs as lt_sample_pass1; LT_EINVAL for target < 1. */
+lt_status lt_sample_pass1_target(lt_ctx* ctx, const lt_frame* f, float rate1, int32_t target, float d_min,
+                                 uint64_t seed, lt_samples* smp);
 /* Pass 2 (Sec. 5, Eq. 3): draws (column by the integer CDF of `weights` or of g when
  * weights is NULL, row uniform) with Philox (t, 0, slice, 2), keeping the first
  * ceil(rate m' n') - n1 new entries.  Appends keys (values undefined until
@@ -374,6 +384,7 @@ typedef struct {
     int32_t adm_iters;
     float adm_alpha_rel;
     float adm_gamma;
+    int32_t target_cut;   /* > 0: pass 1 coarsens to this many columns (lt_sample_pass1_target) */
 } lt_params;
 enum { LT_COMPLETE_ALS = 0, LT_COMPLETE_ADM = 1 };
 

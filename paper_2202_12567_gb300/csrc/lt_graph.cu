@@ -27,12 +27,14 @@ bool params_ok(const lt_params* p) {
            p->lam_rel >= 0.f && (!p->proposal || (p->mix >= 0.f && p->mix <= 1.f)) && p->rank_cols >= 0 &&
            (p->completion == LT_COMPLETE_ALS ||
             (p->completion == LT_COMPLETE_ADM && p->adm_iters >= 0 && p->adm_alpha_rel > 0.f &&
-             p->adm_gamma > 0.f && p->adm_gamma < 1.618f));
+             p->adm_gamma > 0.f && p->adm_gamma < 1.618f)) &&
+           p->target_cut >= 0;
 }
 
 lt_status run_frame(lt_ctx* ctx, const lt_frame* f, const lt_params* p, uint64_t seed, lt_samples* smp,
                     lt_factors* uv, const int32_t* row_perm, float* img) {
-    lt_status st = lt_sample_pass1(ctx, f, p->rate1, p->tau, p->d_min, seed, smp);
+    lt_status st = p->target_cut > 0 ? lt_sample_pass1_target(ctx, f, p->rate1, p->target_cut, p->d_min, seed, smp)
+                                     : lt_sample_pass1(ctx, f, p->rate1, p->tau, p->d_min, seed, smp);
     if (st != LT_OK) return st;
     if (p->rank_cols > 0) {  // per-slice ranks from the coarsened cut
         st = lt_slice_ranks(ctx, f, smp, uv->r, p->rank_cols, uv->rank);

@@ -112,6 +112,7 @@ struct P1Store {
     int32_t* rows;     // [total] row of each storage slot
     float* v0;         // [total]  (V_a, or V_f after a merge)
     float* v1;         // [total]  (V_b), == v0 + total
+    float* v2;         // [total]  V_a kept at a merge (coarsening to a target size), else null
     int64_t total;
 };
 
@@ -262,6 +263,89 @@ __global__ void k_p1_thr(lt_frame F, const float* __restrict__ leafmean, float t
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         thr[s] = tau * t;
+    }
+}
+
+// -- coarsening to a target cut size (Sec. 4): every pair is tested (threshold +inf,
+// so all merge and every internal node gets its cost); then per slice the C - target
+// pairs of smallest effective cost eff(f) = max(cost(f), eff(a), eff(b)) (ties: lower
+// height, lower id) are the merged ones.  Merging by least cost among the testable
+// pairs, one at a time, merges exactly those: a pair becomes testable only after its
+// children merged, and the effective cost is the cost at which the greedy order
+// reaches it.
+__global__ void k_p1_thr_inf(int S, float* thr) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) thr[s] = INFINITY;
+}
+
+__device__ __forceinline__ unsigned long long eff_key(const lt_frame& F, const float* eff, int f) {
+    return (unsigned long long)__float_as_uint(eff[f]) << 32 | (unsigned long long)F.forest[8 * f + 6] << 20 |
+           (unsigned long long)(f - F.C);
+}
+
+__global__ void __launch_bounds__(1024) k_p1_target(lt_frame F, P1Plan pl, float* __restrict__ effs, int target) {
+    __shared__ int32_t hist[256];
+    __shared__ unsigned long long sel[2];
+    __shared__ int32_t krem;
+    const int s = blockIdx.x;
+    const int C = F.C, NF = 2 * C - 1;
+    const int ms = F.slice_off[s + 1] - F.slice_off[s];
+    if (ms == 0) return;
+    const float* cost = pl.cost + (int64_t)s * NF;
+    int32_t* state = pl.state + (int64_t)s * NF;
+    float* eff = effs + (int64_t)s * NF;
+    for (int x = threadIdx.x; x < C; x += blockDim.x) eff[x] = 0.f;
+    __syncthreads();
+    for (int h = 1; h <= F.H; ++h) {
+        for (int i = F.level_off[h] + threadIdx.x; i < F.level_off[h + 1]; i += blockDim.x) {
+            const int f = F.level_nodes[i];
+            eff[f] = fmaxf(cost[f], fmaxf(eff[F.forest[8 * f + 1]], eff[F.forest[8 * f + 2]]));
+        }
+        __syncthreads();
+    }
+    const int K = max(0, min(C - target, C - 1));
+    if (threadIdx.x == 0) {
+        sel[0] = sel[1] = 0ull;
+        krem = K - 1;
+    }
+    __syncthreads();
+    for (int pass = 7; pass >= 0 && K > 0; --pass) {  // radix select of the K-th smallest key
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const unsigned long long prefix = sel[0], mask = sel[1];
+        for (int f = C + threadIdx.x; f < NF; f += blockDim.x) {
+            const unsigned long long key = eff_key(F, eff, f);
+            if ((key & mask) == prefix) atomicAdd(&hist[(key >> (8 * pass)) & 255], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int k = krem, digit = 255;
+            for (int b = 0; b < 256; ++b) {
+                if (k < hist[b]) {
+                    digit = b;
+                    break;
+                }
+                k -= hist[b];
+            }
+            krem = k;
+            sel[0] = prefix | ((unsigned long long)digit << (8 * pass));
+            sel[1] = mask | (255ull << (8 * pass));
+        }
+        __syncthreads();
+    }
+    const unsigned long long pivot = sel[0];
+    auto merged = [&](int x) { return x >= C && K > 0 && eff_key(F, eff, x) <= pivot; };
+    for (int x = threadIdx.x; x < NF; x += blockDim.x) {
+        const bool chosen = x < C || merged(x);
+        const int par = F.forest[8 * x + 3];
+        int stt;
+        if (chosen) {
+            stt = (par >= 0 && merged(par)) ? kStDead : kStAlive;
+        } else {
+            const int a = F.forest[8 * x + 1], b = F.forest[8 * x + 2];
+            const bool ca = a < C || merged(a), cb = b < C || merged(b);
+            stt = (ca && cb) ? kStRejected : kStNot;
+        }
+        state[x] = stt;
     }
 }
 
@@ -487,7 +571,11 @@ __device__ __forceinline__ void decide_pair(const lt_frame& F, const P1Plan& pl,
         const float rfp = __fdiv_rn(If, p_is_a ? Ia : Ib);
         float* fa = st.v0 + pc.iff;
         const float* fb = st.v1 + pc.iff;
-        for (int t = first; t < nf; t += step) fa[t] = (p_is_a ? fa[t] : fb[t]) * rfp;
+        float* keep = st.v2 ? st.v2 + pc.iff : nullptr;
+        for (int t = first; t < nf; t += step) {
+            if (keep) keep[t] = fa[t];
+            fa[t] = (p_is_a ? fa[t] : fb[t]) * rfp;
+        }
     }
     if (writer) {
         cost[pc.f] = cf;
@@ -621,7 +709,9 @@ __global__ void __launch_bounds__(kP1Threads) k_p1_output(lt_frame F, P1Plan pl,
         const int src = from_par ? par : x;
         const int n = cnt[src];
         const int32_t* rr = rows + off[src];
-        const float* vv = (from_par && F.forest[8 * par + 2] == x) ? v1 + off[src] : v0 + off[src];
+        const float* vv = (from_par && F.forest[8 * par + 2] == x) ? v1 + off[src]
+                          : (from_par && st.v2)                   ? st.v2 + base + off[src]
+                                                                  : v0 + off[src];
         float mx = -3.0e38f, mn = 3.0e38f;
         const int dst = (int)(eoff[j]);
         for (int t = lane; t < n; t += 32) {
@@ -972,10 +1062,10 @@ bool samples_ok(const lt_samples* s) {
 
 }  // namespace
 
-extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, float d_min,
-                                     uint64_t seed, lt_samples* smp) {
-    if (!ctx || !frame_ok(f) || !samples_ok(smp) || !(rate1 >= 0.f) || !(tau >= 0.f))
-        return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1: bad arguments");
+namespace {
+
+lt_status sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, int32_t target, float d_min,
+                       uint64_t seed, lt_samples* smp) {
     if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1: no scene uploaded");
     cudaSetDevice(ctx->device);
     const int S = f->S, C = f->C, NF = 2 * C - 1;
@@ -1023,9 +1113,10 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     // then the work arrays of the flat kernels
     const int Hn = f->H + 2;
     const int64_t mcap = std::max<int64_t>(acc, 1024), bcap = std::max<int64_t>((int64_t)S * C, 1024);
-    const size_t store_bytes = (size_t)std::max<int64_t>(acc, 1) * 12 + 1024;
+    const size_t store_bytes = (size_t)std::max<int64_t>(acc, 1) * (target > 0 ? 16 : 12) + 1024;
+    const size_t eff_bytes = target > 0 ? (size_t)S * NF * 4 : 0;
     const size_t work_bytes = (size_t)(S + 1) * 8 + (size_t)S * C * 4 + (size_t)S * 4 + (size_t)Hn * 16 +
-                              (size_t)mcap * 16 + (size_t)bcap * 8 + 16 * 256;
+                              (size_t)mcap * 16 + (size_t)bcap * 8 + eff_bytes + 17 * 256;
     char* q = (char*)lt_scratch(ctx, SCR_P1_STORE, store_bytes + work_bytes, &st);
     if (!q) return st;
     P1Store store;
@@ -1033,6 +1124,7 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     store.rows = (int32_t*)q;
     store.v0 = (float*)(q + ((acc * 4 + 255) & ~255LL));
     store.v1 = store.v0 + acc;
+    store.v2 = target > 0 ? store.v1 + acc : nullptr;
     char* wp = q + ((store_bytes + 255) & ~(size_t)255);
     auto wtake = [&](size_t nbytes) {
         char* r = wp;
@@ -1051,6 +1143,7 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     w.big = (int64_t*)wtake((size_t)bcap * 8);
     w.mcap = mcap;
     w.bcap = bcap;
+    float* effs = target > 0 ? (float*)wtake(eff_bytes) : nullptr;
     if ((size_t)(wp - q) > ctx->scr_size[SCR_P1_STORE])
         return lt_fail(ctx, LT_ENOMEM, "lt_sample_pass1: work layout overflow");
     LT_CUDA(ctx, cudaMemsetAsync(w.mcount, 0, (size_t)Hn * 8, ctx->stream));
@@ -1070,8 +1163,13 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
     LT_LAUNCH_CHECK(ctx, "k_p1_initial");
     k_p1_leafmean<<<grid_for((int64_t)S * C, 256), 256, 0, ctx->stream>>>(*f, pl, store, w.leafmean);
     LT_LAUNCH_CHECK(ctx, "k_p1_leafmean");
-    k_p1_thr<<<S, 256, 0, ctx->stream>>>(*f, w.leafmean, tau, w.thr);
-    LT_LAUNCH_CHECK(ctx, "k_p1_thr");
+    if (target > 0) {
+        k_p1_thr_inf<<<(S + 255) / 256, 256, 0, ctx->stream>>>(S, w.thr);
+        LT_LAUNCH_CHECK(ctx, "k_p1_thr_inf");
+    } else {
+        k_p1_thr<<<S, 256, 0, ctx->stream>>>(*f, w.leafmean, tau, w.thr);
+        LT_LAUNCH_CHECK(ctx, "k_p1_thr");
+    }
     std::vector<int32_t> loff(f->H + 2, 0);
     if (ctx->use_plan) {
         if ((int)ctx->plan.level_off.size() != f->H + 2)
@@ -1098,12 +1196,32 @@ extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1
         k_p1_decide_big<<<4 * nsm, 256, 0, ctx->stream>>>(*f, pl, store, w, h);
         LT_LAUNCH_CHECK(ctx, "k_p1_decide_big");
     }
+    if (target > 0) {
+        k_p1_target<<<S, 1024, 0, ctx->stream>>>(*f, pl, effs, target);
+        LT_LAUNCH_CHECK(ctx, "k_p1_target");
+    }
     const size_t shm = (size_t)C * 4;
     if (shm > 16 * 1024)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_p1_output, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     k_p1_output<<<S, kP1Threads, shm, ctx->stream>>>(*f, pl, store, *smp, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_p1_output");
     return LT_OK;
+}
+
+}  // namespace
+
+extern "C" lt_status lt_sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, float d_min,
+                                     uint64_t seed, lt_samples* smp) {
+    if (!ctx || !frame_ok(f) || !samples_ok(smp) || !(rate1 >= 0.f) || !(tau >= 0.f))
+        return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1: bad arguments");
+    return sample_pass1(ctx, f, rate1, tau, 0, d_min, seed, smp);
+}
+
+extern "C" lt_status lt_sample_pass1_target(lt_ctx* ctx, const lt_frame* f, float rate1, int32_t target,
+                                            float d_min, uint64_t seed, lt_samples* smp) {
+    if (!ctx || !frame_ok(f) || !samples_ok(smp) || !(rate1 >= 0.f) || target < 1)
+        return lt_fail(ctx, LT_EINVAL, "lt_sample_pass1_target: bad arguments");
+    return sample_pass1(ctx, f, rate1, 0.f, target, d_min, seed, smp);
 }
 
 extern "C" lt_status lt_sample_pass2(lt_ctx* ctx, const lt_frame* f, const float* weights, float rate,

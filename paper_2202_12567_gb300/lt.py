@@ -62,7 +62,8 @@ class lt_rgb(ctypes.Structure):
 class lt_params(ctypes.Structure):
     _fields_ = [("rate1", _f32), ("tau", _f32), ("d_min", _f32), ("rate", _f32), ("als_iters", _i32),
                 ("lam_rel", _f32), ("weights", _p), ("proposal", _p), ("mix", _f32), ("rank_cols", _i32),
-                ("completion", _i32), ("adm_iters", _i32), ("adm_alpha_rel", _f32), ("adm_gamma", _f32)]
+                ("completion", _i32), ("adm_iters", _i32), ("adm_alpha_rel", _f32), ("adm_gamma", _f32),
+                ("target_cut", _i32)]
 
 
 COMPLETE_ALS, COMPLETE_ADM = 0, 1
@@ -95,6 +96,8 @@ _SIGS = {
     "lt_make_slices": (_i32, [_p, _p, _i64, _i32, _i32, _f32, _p, _p]),
     "lt_permute_points": (_i32, [_p, _p, _i64, _p, _p]),
     "lt_sample_pass1": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, _f32, _f32, _u64, ctypes.POINTER(lt_samples)]),
+    "lt_sample_pass1_target": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, _i32, _f32, _u64,
+                                      ctypes.POINTER(lt_samples)]),
     "lt_sample_pass2": (_i32, [_p, ctypes.POINTER(lt_frame), _p, _f32, _u64, ctypes.POINTER(lt_samples)]),
     "lt_eval_entries": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples)]),
     "lt_eval_stats": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples), _p]),
@@ -442,6 +445,12 @@ def lt_sample_pass1(ctx: Context, frame: Frame, smp: Samples, rate, tau, d_min, 
                                                           seed, ctypes.byref(smp.struct())))
 
 
+def lt_sample_pass1_target(ctx: Context, frame: Frame, smp: Samples, rate1, target, d_min, seed):
+    ctx._check("lt_sample_pass1_target", ctx.lib.lt_sample_pass1_target(ctx.h, ctypes.byref(frame.struct()), rate1,
+                                                                        int(target), d_min, seed,
+                                                                        ctypes.byref(smp.struct())))
+
+
 def lt_sample_pass2(ctx: Context, frame: Frame, smp: Samples, rate, seed, weights=None):
     ctx._check("lt_sample_pass2", ctx.lib.lt_sample_pass2(ctx.h, ctypes.byref(frame.struct()), _ptr(weights), rate,
                                                           seed, ctypes.byref(smp.struct())))
@@ -533,7 +542,8 @@ def params(cfg: dict, weights=None, proposal=None, mix: float = 0.8) -> lt_param
     return lt_params(cfg["rate1"], cfg["tau"], cfg["d_min"], cfg["rate"], cfg["als_iters"], cfg["lam_rel"],
                      _ptr(weights), _ptr(proposal), mix, int(cfg.get("rank_cols", 0)),
                      COMPLETE_ADM if adm else COMPLETE_ALS, int(cfg.get("adm_iters", 100)),
-                     float(cfg.get("adm_alpha_rel", 0.3)), float(cfg.get("adm_gamma", 1.0)))
+                     float(cfg.get("adm_alpha_rel", 0.3)), float(cfg.get("adm_gamma", 1.0)),
+                     int(cfg.get("target_cut", 0)))
 
 
 def lt_slice_ranks(ctx: Context, frame: Frame, smp: Samples, R: int, cols: int, rank=None):

@@ -73,7 +73,10 @@ class Renderer:
     # ---------------------------------------------------------------- frame stages
     def pass1(self, seed):
         c = self.cfg
-        lt.lt_sample_pass1(self.ctx, self.frame, self.smp, c["rate1"], c["tau"], c["d_min"], seed)
+        if int(c.get("target_cut", 0)) > 0:  # coarsen to a target cut size (Sec. 4)
+            lt.lt_sample_pass1_target(self.ctx, self.frame, self.smp, c["rate1"], c["target_cut"], c["d_min"], seed)
+        else:
+            lt.lt_sample_pass1(self.ctx, self.frame, self.smp, c["rate1"], c["tau"], c["d_min"], seed)
 
     def pass2(self, seed, weights=None):
         lt.lt_sample_pass2(self.ctx, self.frame, self.smp, self.cfg["rate"], seed, weights)
