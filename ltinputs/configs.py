@@ -21,6 +21,7 @@ import copy
 #   lam_rel   ridge term relative to the mean Gram diagonal
 #   slicing   "kmeans" (n_slices clusters) or "split6d" (the paper's recursive 6-D
 #             binary split into slices of at most slice_size pixels)
+#   n_meshes  icosphere occluders (triangles, mesh_subdiv subdivisions) besides the boxes
 #   completion  "als" (masked ALS) or "adm" (the nonnegative ADM of App. A) with
 #             adm_iters iterations, penalties adm_alpha_rel times the start's mean
 #             Gram diagonal, and step gamma adm_gamma
@@ -87,4 +88,13 @@ CONFIGS["room256_vpl16k_2box"] = dict(
 # (the paper's coloured scenes); the three channels are stacked as rows of a slice.
 CONFIGS["room256_vpl16k_2box_rgb"] = dict(
     CONFIGS["room256_vpl16k_2box"], rgb=True, light_rgb=(1.0, 0.85, 0.7),
+)
+
+# Triangle-mesh occluders: icospheres (320 triangles each) on the floor besides the
+# two boxes; the tiny form for the oracle, the full form at the bench size.
+CONFIGS["room64_vpl1k_mesh"] = dict(
+    CONFIGS["room64_vpl1k_2box"], n_meshes=2, mesh_subdiv=2, scene_seed=1004,
+)
+CONFIGS["room256_vpl16k_mesh"] = dict(
+    CONFIGS["room256_vpl16k_2box"], n_meshes=6, mesh_subdiv=3, scene_seed=5001,
 )

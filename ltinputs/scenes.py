@@ -27,6 +27,12 @@ and the light has colour cfg["light_rgb"]; the scalar albedo and flux then becom
 the Rec. 709 luminances of the colours, and ``Scene.rgb`` holds point_albedo [m, 3],
 vpl_albedo [n, 3] and vpl_flux [n, 3] (float32).
 
+Meshes (cfg["n_meshes"] > 0): that many icospheres (the icosahedron subdivided
+cfg["mesh_subdiv"] times, vertices pushed to the sphere) stand on the floor as
+triangle occluders; each sphere is one material (face id after the boxes' faces),
+shading points and VPLs on it take the flat normal of the triangle they hit, facing
+the incoming ray.  ``Scene.tris`` holds them as [nt, 3, 3] float32.
+
 Everything here is input generation: the nearest-hit ray caster below only places
 points and lights.  It uses numpy's PCG64 generator seeded per scene.
 """
@@ -55,6 +61,12 @@ class Scene:
     height: int
     n_emitted: int
     rgb: dict | None = None    # colour arrays of an RGB scene (see the module notes)
+    tris: np.ndarray | None = None  # [nt, 3, 3] triangle occluders of a mesh scene
+
+    @property
+    def occluders(self):
+        """What shadow rays test: the boxes, or (boxes, triangles) in a mesh scene."""
+        return self.boxes if self.tris is None else (self.boxes, self.tris)
 
     @property
     def m(self) -> int:
@@ -88,6 +100,83 @@ def _make_boxes(cfg: dict, rng: np.random.Generator) -> np.ndarray:
     if not boxes:
         return np.zeros((0, 6), dtype=np.float32)
     return np.asarray(boxes, dtype=np.float32)
+
+
+_ICO_T = (1.0 + 5.0 ** 0.5) / 2.0
+_ICO_V = [(-1, _ICO_T, 0), (1, _ICO_T, 0), (-1, -_ICO_T, 0), (1, -_ICO_T, 0), (0, -1, _ICO_T), (0, 1, _ICO_T),
+          (0, -1, -_ICO_T), (0, 1, -_ICO_T), (_ICO_T, 0, -1), (_ICO_T, 0, 1), (-_ICO_T, 0, -1), (-_ICO_T, 0, 1)]
+_ICO_F = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+          (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+          (8, 6, 7), (9, 8, 1)]
+
+
+def icosphere(subdiv: int) -> np.ndarray:
+    """Triangles [nt, 3, 3] of the unit icosphere: each subdivision splits a triangle
+    into four at its edge midpoints, pushed out to the sphere."""
+    verts = [np.array(v, dtype=np.float64) / np.linalg.norm(v) for v in _ICO_V]
+    faces = list(_ICO_F)
+    for _ in range(subdiv):
+        mid = {}
+
+        def m(i, j):
+            key = (min(i, j), max(i, j))
+            if key not in mid:
+                v = verts[i] + verts[j]
+                verts.append(v / np.linalg.norm(v))
+                mid[key] = len(verts) - 1
+            return mid[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = m(a, b), m(b, c), m(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.array(verts)
+    return V[np.array(faces)]
+
+
+def _make_meshes(cfg: dict, rng: np.random.Generator, boxes: np.ndarray) -> np.ndarray | None:
+    n = int(cfg.get("n_meshes", 0))
+    if n <= 0:
+        return None
+    unit = icosphere(int(cfg.get("mesh_subdiv", 2)))
+    out = []
+    for k in range(n):
+        r = rng.uniform(0.07, 0.14)
+        cx = (k + 0.5) / n + rng.uniform(-0.05, 0.05)
+        cx = float(np.clip(cx, r + 0.02, 1 - r - 0.02))
+        cz = rng.uniform(0.3 + r, 0.9 - r)
+        cy = r + rng.uniform(0.0, 0.25)
+        out.append(unit * r + np.array([cx, cy, cz]))
+    return np.concatenate(out).astype(np.float32)
+
+
+def _tri_nearest(org, d, tris, chunk=1024):
+    """Nearest hit of rays with the triangles (float64 Moller-Trumbore): (t, index)."""
+    nr = org.shape[0]
+    t_out = np.full(nr, np.inf)
+    i_out = np.full(nr, -1, dtype=np.int64)
+    T = tris.astype(np.float64)
+    v0, e1, e2 = T[:, 0], T[:, 1] - T[:, 0], T[:, 2] - T[:, 0]
+    for s in range(0, nr, chunk):
+        e = min(nr, s + chunk)
+        D = d[s:e, None, :]
+        p = np.cross(D, e2[None])
+        det = np.sum(e1[None] * p, axis=-1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / det
+            sv = org[s:e, None, :] - v0[None]
+            u = np.sum(sv * p, axis=-1) * inv
+            q = np.cross(sv, e1[None])
+            v = np.sum(D * q, axis=-1) * inv
+            t = np.sum(e2[None] * q, axis=-1) * inv
+        ok = (det != 0) & (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t > 1e-7)
+        t = np.where(ok, t, np.inf)
+        j = np.argmin(t, axis=1)
+        tj = t[np.arange(e - s), j]
+        t_out[s:e] = tj
+        i_out[s:e] = np.where(np.isfinite(tj), j, -1)
+    return t_out, i_out
 
 
 def _materials(n_faces: int, glossy_frac: float, rng: np.random.Generator):
@@ -186,20 +275,47 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
     boxes = _make_boxes(cfg, rng)
     nb = boxes.shape[0]
     albedo, gloss = _materials(5 + 6 * nb, float(cfg.get("glossy_frac", 0.0)), rng)
+    # meshes draw from their own stream, so the scenes without them are unchanged
+    mrng = np.random.default_rng(seed + 104729)
+    tris = _make_meshes(cfg, mrng, boxes)
+    n_mesh = int(cfg.get("n_meshes", 0)) if tris is not None else 0
+    per_mesh = tris.shape[0] // max(n_mesh, 1) if tris is not None else 0
+    if n_mesh:
+        ma, mg = _materials(n_mesh, float(cfg.get("glossy_frac", 0.0)), mrng)
+        albedo, gloss = np.concatenate([albedo, ma]), np.concatenate([gloss, mg])
     colour = bool(cfg.get("rgb", False))
     if colour:
         face_rgb = np.random.default_rng(seed + 7919).uniform(0.2, 0.8, size=(5 + 6 * nb, 3))
+        if n_mesh:
+            face_rgb = np.concatenate([face_rgb, mrng.uniform(0.2, 0.8, size=(n_mesh, 3))])
         albedo = face_rgb @ LUMINANCE
         light_rgb = np.asarray(cfg.get("light_rgb", (1.0, 0.85, 0.7)), dtype=np.float64)
+
+    def hit(o, dd):
+        """Nearest hit over walls, boxes and triangles: (t, face, normal)."""
+        t, face = _nearest_hit(o, dd, boxes)
+        nrm = np.zeros((t.shape[0], 3))
+        if tris is not None:
+            tt, ti = _tri_nearest(o, dd, tris)
+            closer = tt < t
+            t = np.where(closer, tt, t)
+            face = np.where(closer, 5 + 6 * nb + ti // per_mesh, face)
+            T = tris[ti[closer]].astype(np.float64)
+            n = np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0])
+            n /= np.linalg.norm(n, axis=1, keepdims=True)
+            n = np.where(np.sum(n * dd[closer], axis=1, keepdims=True) > 0, -n, n)
+            nrm[closer] = n
+        flat = face < 5 + 6 * nb
+        nrm[flat & (face >= 0)] = _face_normals(face[flat & (face >= 0)])
+        return t, face, nrm
 
     # shading points
     width, height = int(cfg["width"]), int(cfg["height"])
     org, d = _camera_rays(width, height)
-    t, face = _nearest_hit(org, d, boxes)
+    t, face, nrm = hit(org, d)
     if np.any(face < 0):
         raise RuntimeError("a camera ray missed the room")
     pos = org + t[:, None] * d
-    nrm = _face_normals(face)
     m = pos.shape[0]
     points = np.zeros((3, m, 4), dtype=np.float32)
     points[0, :, :3] = pos
@@ -212,7 +328,7 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
     n = int(cfg["n_vpl"])
     half = float(cfg.get("light_size", 0.2)) / 2
     power = float(cfg.get("light_power", 1.0))
-    hits_pos, hits_face, hits_dir = [], [], []
+    hits_pos, hits_face, hits_dir, hits_nrm = [], [], [], []
     n_hit = 0
     n_emitted = 0
     batch = max(1024, n)
@@ -223,7 +339,7 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
         sin_t = np.sqrt(r[:, 3])
         cos_t = np.sqrt(1 - r[:, 3])
         dd = np.stack([sin_t * np.cos(phi), -cos_t, sin_t * np.sin(phi)], axis=1)
-        tt, ff = _nearest_hit(lo, dd, boxes)
+        tt, ff, nn = hit(lo, dd)
         ok = ff >= 0
         # keep emission order so that N_emitted is well defined
         idx = np.nonzero(ok)[0]
@@ -237,14 +353,16 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
         hits_pos.append(lo[idx] + tt[idx, None] * dd[idx])
         hits_face.append(ff[idx])
         hits_dir.append(-dd[idx])
+        hits_nrm.append(nn[idx])
         n_hit += idx.shape[0]
     vpos = np.concatenate(hits_pos)[:n]
     vface = np.concatenate(hits_face)[:n]
     vdir = np.concatenate(hits_dir)[:n]
+    vnrm = np.concatenate(hits_nrm)[:n]
     vpls = np.zeros((3, n, 4), dtype=np.float32)
     vpls[0, :, :3] = vpos
     vpls[0, :, 3] = albedo[vface]
-    vpls[1, :, :3] = _face_normals(vface)
+    vpls[1, :, :3] = vnrm
     vpls[1, :, 3] = gloss[vface]
     vpls[2, :, :3] = vdir
     vpls[2, :, 3] = power / n_emitted
@@ -255,7 +373,7 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
                    vpl_albedo=face_rgb[vface].astype(np.float32),
                    vpl_flux=np.broadcast_to(power / n_emitted * light_rgb, (n, 3)).astype(np.float32))
     return Scene(cfg=cfg, boxes=boxes, points=points, vpls=vpls, width=width, height=height,
-                 n_emitted=int(n_emitted), rgb=rgb)
+                 n_emitted=int(n_emitted), rgb=rgb, tris=tris)
 
 
 def single_quad_scene(vpl_pos, vpl_nrm, vpl_flux, vpl_albedo, quad_y: float, res: int,

@@ -60,7 +60,7 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
     tree, forest, pts_s = st["tree"], st["forest"], st["pts_s"]
     a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
     m_s = b - a
-    p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.boxes, s, a, m_s, cfg["rate1"],
+    p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.occluders, s, a, m_s, cfg["rate1"],
                              cfg["tau"], seed, cfg["d_min"], order_rng, target=target_cut(cfg))
     n_s = p1.col_node.size
     w = p1.g if weights is None else weights
@@ -68,7 +68,7 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
     if r2.size:
         nodes = p1.col_node[c2]
         v2 = shading.node_entries(pts_s, scene.vpls, a + r2, tree.rep[nodes],
-                                  node_scale(tree, scene.vpls, nodes), scene.boxes, cfg["d_min"])
+                                  node_scale(tree, scene.vpls, nodes), scene.occluders, cfg["d_min"])
     else:
         v2 = np.zeros(0)
     res = SliceResult(p1=p1, p2_rows=r2, p2_cols=c2, p2_vals=v2, U=None, V=None, hit_cap=hit_cap)

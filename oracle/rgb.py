@@ -117,14 +117,14 @@ def render_frame(scene, cfg, st, seed=None):
     for s in range(S):
         a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
         m_s = b - a
-        p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.boxes, s, a, m_s, cfg["rate1"], cfg["tau"],
+        p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.occluders, s, a, m_s, cfg["rate1"], cfg["tau"],
                                  seed, cfg["d_min"], target=pipeline.target_cut(cfg))
         n_s = p1.col_node.size
         r2, c2, _, _ = pass2.draw_pass2(seed, s, m_s, p1.g, p1.rows * n_s + p1.cols, cfg["rate"])
         rows = np.concatenate([p1.rows, r2]).astype(np.int64)
         cols = np.concatenate([p1.cols, c2]).astype(np.int64)
         vals = node_entries(pts_s, scene.vpls, scene.rgb, st["row_perm"], tree, a + rows, p1.col_node[cols],
-                            scene.boxes, cfg["d_min"])
+                            scene.occluders, cfg["d_min"])
         factors.append(complete_stacked(rows, cols, vals, m_s, n_s, cfg["rank"], cfg, seed, s))
         omega.append((rows, cols, p1.col_node, vals))
     return render_stacked(factors, st["row_perm"], st["slice_off"], scene.m), omega

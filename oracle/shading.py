@@ -80,11 +80,49 @@ def unoccluded(points, vpls, rows, cols, d_min=0.01):
     return flux * f_p * f_q * G
 
 
+def segment_hits_triangles(o, e, tris):
+    """True where the segment o + t (e - o), t in (T_MIN, T_MAX), meets a closed
+    triangle (Moller-Trumbore in float64; a segment in a triangle's plane does not
+    hit it).  tris [nt, 3, 3].  Tests every triangle."""
+    o = np.asarray(o, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    k = o.shape[0]
+    hit = np.zeros(k, dtype=bool)
+    T = np.asarray(tris, dtype=np.float64)
+    if T.shape[0] == 0 or k == 0:
+        return hit
+    v0, e1, e2 = T[:, 0], T[:, 1] - T[:, 0], T[:, 2] - T[:, 0]
+    D = e - o
+    chunk = max(1, 2_000_000 // T.shape[0])
+    for s in range(0, k, chunk):
+        DD = D[s:s + chunk, None, :]
+        p = np.cross(DD, e2[None])
+        det = np.sum(e1[None] * p, axis=-1)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            inv = 1.0 / det
+            sv = o[s:s + chunk, None, :] - v0[None]
+            u = np.sum(sv * p, axis=-1) * inv
+            q = np.cross(sv, e1[None])
+            v = np.sum(DD * q, axis=-1) * inv
+            t = np.sum(e2[None] * q, axis=-1) * inv
+        ok = (det != 0) & (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t > T_MIN) & (t < T_MAX)
+        hit[s:s + chunk] = np.any(ok, axis=1)
+    return hit
+
+
 def segment_blocked(o, e, boxes):
-    """True where the segment o + t (e - o), t in (T_MIN, T_MAX), meets a closed box.
+    """True where the segment o + t (e - o), t in (T_MIN, T_MAX), meets a closed box
+    (or, when ``boxes`` is a pair (boxes, triangles), a box or a triangle).
 
     o, e: [k, 3] float64; boxes [nb, 6].  Tests every box (slab method).
     """
+    if isinstance(boxes, tuple):
+        bx, tris = boxes
+        blocked = segment_blocked(o, e, bx)
+        rest = ~blocked
+        if np.any(rest):
+            blocked[rest] = segment_hits_triangles(np.asarray(o)[rest], np.asarray(e)[rest], tris)
+        return blocked
     o = np.asarray(o, dtype=np.float64)
     e = np.asarray(e, dtype=np.float64)
     k = o.shape[0]

@@ -554,3 +554,56 @@ def test_target_order_is_the_effective_cost_order():
     for T in (700, 400, 150, 30):
         r = run(target=T)
         assert {e[0] for e in r.log} == set(order[:C - T])
+
+
+# ---------------------------------------------------------------- triangle occluders
+def _box_triangles(b):
+    """The 12 triangles of the closed box b = [lo xyz, hi xyz]."""
+    lo, hi = np.asarray(b[:3], float), np.asarray(b[3:], float)
+    c = np.array([[lo[0] if i & 1 == 0 else hi[0], lo[1] if i & 2 == 0 else hi[1], lo[2] if i & 4 == 0 else hi[2]]
+                  for i in range(8)])
+    quads = [(0, 1, 3, 2), (4, 5, 7, 6), (0, 1, 5, 4), (2, 3, 7, 6), (0, 2, 6, 4), (1, 3, 7, 5)]
+    out = []
+    for q0, q1, q2, q3 in quads:
+        out.append([c[q0], c[q1], c[q2]])
+        out.append([c[q0], c[q2], c[q3]])
+    return np.array(out)
+
+
+def test_box_as_triangles_blocks_the_same_segments():
+    rng = np.random.default_rng(5)
+    box = np.array([[0.3, 0.2, 0.4, 0.6, 0.5, 0.7]])
+    o = rng.uniform(0, 1, (20000, 3))
+    e = rng.uniform(0, 1, (20000, 3))
+    inside = lambda x: np.all((x >= box[0, :3]) & (x <= box[0, 3:]), axis=1)
+    keep = ~inside(o) & ~inside(e)  # a solid box also blocks a segment inside it, a surface does not
+    o, e = o[keep], e[keep]
+    by_box = shading.segment_blocked(o, e, box)
+    by_tris = shading.segment_hits_triangles(o, e, _box_triangles(box[0]))
+    assert by_box.sum() > 1000
+    assert np.array_equal(by_box, by_tris)
+    # the pair form tests both
+    assert np.array_equal(shading.segment_blocked(o, e, (np.zeros((0, 6)), _box_triangles(box[0]))), by_box)
+
+
+def test_single_triangle_cases():
+    tri = np.array([[[0.0, 0.0, 0.5], [1.0, 0.0, 0.5], [0.0, 1.0, 0.5]]])
+    o = np.array([[0.2, 0.2, 0.0], [0.8, 0.8, 0.0], [0.2, 0.2, 0.0], [0.2, 0.2, 0.5], [0.2, 0.2, 0.6]])
+    e = np.array([[0.2, 0.2, 1.0], [0.8, 0.8, 1.0], [0.2, 0.2, 0.4], [0.9, 0.0, 0.5], [0.2, 0.2, 1.0]])
+    # through the inside; outside the hypotenuse; ends before the plane; in the plane; starts behind it
+    assert shading.segment_hits_triangles(o, e, tri).tolist() == [True, False, False, False, False]
+
+
+def test_mesh_scene_full_sampling_reproduces_bruteforce():
+    """The triangle occluders enter every shadow ray of the pipeline: at full sampling
+    and full rank the frame equals the brute force over the mesh scene."""
+    cfg = get_config("room64_vpl1k_mesh", width=8, height=8, n_vpl=12, n_slices=2, rate=1.0, eps_cut=0.0,
+                     max_cut=100, tau=0.0, lam_rel=1e-13, als_iters=2, rank=12, rate1=1.0, mesh_subdiv=1)
+    sc = make_scene(cfg)
+    assert sc.tris is not None and sc.tris.shape[0] == 160
+    ref = bruteforce.render(sc.points, sc.vpls, sc.occluders)
+    nobox = bruteforce.render(sc.points, sc.vpls, sc.boxes)
+    assert not np.allclose(ref, nobox)  # the spheres cast shadows
+    img, _ = pipeline.render_frame(sc, cfg)
+    # full-rank ALS on 32 x 12 slices with a 1e-13 ridge: exact up to its conditioning
+    np.testing.assert_allclose(img, ref, rtol=1e-6, atol=1e-6 * ref.max())
