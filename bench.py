@@ -237,6 +237,43 @@ def rgb_leg(args, device: int, flush) -> dict | None:
     return out
 
 
+def mesh_leg(args, device: int, flush) -> dict | None:
+    """The workload with triangle-mesh occluders (icospheres through a BVH) besides the
+    boxes, plain calls on a context of its own: ms/frame and rel-RMSE against the GPU
+    brute force of the same scene."""
+    import torch
+
+    from ltinputs import CONFIGS, get_config, make_scene
+    from paper_2202_12567_gb300 import lt
+    from paper_2202_12567_gb300.renderer import Renderer
+    name = args.workload.replace("_2box", "_mesh")
+    if name == args.workload or name not in CONFIGS:
+        return None
+    cfg = get_config(name)
+    sc = make_scene(cfg)
+    R = Renderer(sc, cfg, device=device).setup()
+    for k in range(2):
+        R.render(seed=cfg["frame_seed"] + k)
+    ts = []
+    for k in range(max(3, args.steps // 4)):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        R.render(seed=cfg["frame_seed"] + 100 + k, sync=False)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    img = R.img.double()
+    ref = R.bruteforce().double()
+    rel = float(torch.linalg.norm(img - ref) / torch.linalg.norm(ref))
+    lt.lt_sync(R.ctx)
+    return dict(workload=f"{name}: {sc.tris.shape[0]} triangles ({cfg['n_meshes']} icospheres) and "
+                         f"{sc.nb} boxes as occluders",
+                ms_per_frame=round(statistics.mean(ts), 3), rel_rmse_vs_bruteforce=round(rel, 5),
+                rays_per_pixel=round(float(R.rays()) / R.frame.m, 2))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -446,6 +483,7 @@ def run_ours(args):
     roof = als_roofline(lt, ctx, R, half_ms)
     roof_eval = eval_roofline(lt, ctx, R, stage_ms, clk)
     colour = rgb_leg(args, local, flush)
+    meshes = mesh_leg(args, local, flush)
 
     line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
@@ -468,6 +506,7 @@ def run_ours(args):
                             eval_roofline=roof_eval,
                             adm_completion=adm,
                             rgb=colour,
+                            mesh=meshes,
                             setup_ms=round(setup_ms, 1),
                             stage_ms=dict(zip(["pass1", "pass2", "eval", "complete", "render"],
                                               [round(x, 4) for x in stage_ms.tolist()]))),

@@ -131,8 +131,21 @@ lt_status lt_debug_scratch(lt_ctx* ctx, int32_t slot, void** ptr, int64_t* bytes
  * on the host from a copy of the boxes and kept in the context.  nb may be 0. */
 lt_status lt_scene_upload(lt_ctx* ctx, const float* boxes, int64_t nb, int32_t grid_res);
 
+/* Triangle occluders besides the boxes (synthetic mesh scenes; the paper casts its
+ * shadow rays through an SBVH over triangles, Sec. 6): tris[nt][9] (three vertices,
+ * device float32) are copied into a linear BVH (Morton codes of the centroids,
+ * Karras topology, bottom-up boxes); from then on every shadow test of the context
+ * also tests the triangles (closed triangles, Moller-Trumbore, t in (1e-4, 1 -
+ * 1e-4)).  Call after lt_scene_upload, which clears the triangles; nt = 0 clears them
+ * too.  Synchronous.  LT_EINVAL while frame graphs of the context are alive. */
+lt_status lt_mesh_upload(lt_ctx* ctx, const float* tris, int64_t nt);
+/* Copies of the BVH for inspection (device buffers): aabb[2nt-1][6], child[nt-1][2]
+ * (node ids; leaf j is node nt-1+j), leaf_tri[nt]. */
+lt_status lt_mesh_bvh(const lt_ctx* ctx, float* aabb, int32_t* child, int32_t* leaf_tri);
+
 /* Shadow test of k segments org[k][3] -> end[k][3] over t in (1e-4, 1 - 1e-4):
- * blocked[k] = 1 if a closed box meets it (no offsets applied). */
+ * blocked[k] = 1 if a closed box or an uploaded triangle meets it (no offsets
+ * applied). */
 lt_status lt_shadow_test(lt_ctx* ctx, const float* org, const float* end, int64_t k,
                          uint8_t* blocked);
 

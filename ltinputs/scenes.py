@@ -135,47 +135,64 @@ def icosphere(subdiv: int) -> np.ndarray:
     return V[np.array(faces)]
 
 
-def _make_meshes(cfg: dict, rng: np.random.Generator, boxes: np.ndarray) -> np.ndarray | None:
+def _make_meshes(cfg: dict, rng: np.random.Generator, boxes: np.ndarray):
+    """(triangles [nt, 3, 3] float32, bounding spheres [(centre, radius)]) or (None, [])."""
     n = int(cfg.get("n_meshes", 0))
     if n <= 0:
-        return None
+        return None, []
     unit = icosphere(int(cfg.get("mesh_subdiv", 2)))
-    out = []
+    out, spheres = [], []
     for k in range(n):
         r = rng.uniform(0.07, 0.14)
         cx = (k + 0.5) / n + rng.uniform(-0.05, 0.05)
         cx = float(np.clip(cx, r + 0.02, 1 - r - 0.02))
         cz = rng.uniform(0.3 + r, 0.9 - r)
         cy = r + rng.uniform(0.0, 0.25)
-        out.append(unit * r + np.array([cx, cy, cz]))
-    return np.concatenate(out).astype(np.float32)
+        centre = np.array([cx, cy, cz])
+        out.append(unit * r + centre)
+        spheres.append((centre, r))
+    return np.concatenate(out).astype(np.float32), spheres
 
 
-def _tri_nearest(org, d, tris, chunk=1024):
-    """Nearest hit of rays with the triangles (float64 Moller-Trumbore): (t, index)."""
+def _tri_nearest(org, d, tris, spheres, chunk=1024):
+    """Nearest hit of rays with the triangles (float64 Moller-Trumbore): (t, index).
+    Each mesh is tested only against the rays that meet its bounding sphere."""
     nr = org.shape[0]
     t_out = np.full(nr, np.inf)
     i_out = np.full(nr, -1, dtype=np.int64)
     T = tris.astype(np.float64)
-    v0, e1, e2 = T[:, 0], T[:, 1] - T[:, 0], T[:, 2] - T[:, 0]
-    for s in range(0, nr, chunk):
-        e = min(nr, s + chunk)
-        D = d[s:e, None, :]
-        p = np.cross(D, e2[None])
-        det = np.sum(e1[None] * p, axis=-1)
-        with np.errstate(divide="ignore", invalid="ignore"):
-            inv = 1.0 / det
-            sv = org[s:e, None, :] - v0[None]
-            u = np.sum(sv * p, axis=-1) * inv
-            q = np.cross(sv, e1[None])
-            v = np.sum(D * q, axis=-1) * inv
-            t = np.sum(e2[None] * q, axis=-1) * inv
-        ok = (det != 0) & (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t > 1e-7)
-        t = np.where(ok, t, np.inf)
-        j = np.argmin(t, axis=1)
-        tj = t[np.arange(e - s), j]
-        t_out[s:e] = tj
-        i_out[s:e] = np.where(np.isfinite(tj), j, -1)
+    per = T.shape[0] // max(len(spheres), 1)
+    for m, (c, r) in enumerate(spheres):
+        # rays through the (slightly inflated) bounding sphere
+        oc = org - c
+        b = np.sum(oc * d, axis=1)
+        cc = np.sum(oc * oc, axis=1) - (1.001 * r) ** 2
+        dd2 = np.sum(d * d, axis=1)
+        disc = b * b - dd2 * cc
+        rays = np.nonzero(disc >= 0)[0]
+        if rays.size == 0:
+            continue
+        Tm = T[m * per:(m + 1) * per]
+        v0, e1, e2 = Tm[:, 0], Tm[:, 1] - Tm[:, 0], Tm[:, 2] - Tm[:, 0]
+        for s in range(0, rays.size, chunk):
+            idx = rays[s:s + chunk]
+            D = d[idx, None, :]
+            p = np.cross(D, e2[None])
+            det = np.sum(e1[None] * p, axis=-1)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                inv = 1.0 / det
+                sv = org[idx, None, :] - v0[None]
+                u = np.sum(sv * p, axis=-1) * inv
+                q = np.cross(sv, e1[None])
+                v = np.sum(D * q, axis=-1) * inv
+                t = np.sum(e2[None] * q, axis=-1) * inv
+            ok = (det != 0) & (u >= 0) & (u <= 1) & (v >= 0) & (u + v <= 1) & (t > 1e-7)
+            t = np.where(ok, t, np.inf)
+            j = np.argmin(t, axis=1)
+            tj = t[np.arange(idx.size), j]
+            better = tj < t_out[idx]
+            t_out[idx] = np.where(better, tj, t_out[idx])
+            i_out[idx] = np.where(better, m * per + j, i_out[idx])
     return t_out, i_out
 
 
@@ -277,7 +294,7 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
     albedo, gloss = _materials(5 + 6 * nb, float(cfg.get("glossy_frac", 0.0)), rng)
     # meshes draw from their own stream, so the scenes without them are unchanged
     mrng = np.random.default_rng(seed + 104729)
-    tris = _make_meshes(cfg, mrng, boxes)
+    tris, spheres = _make_meshes(cfg, mrng, boxes)
     n_mesh = int(cfg.get("n_meshes", 0)) if tris is not None else 0
     per_mesh = tris.shape[0] // max(n_mesh, 1) if tris is not None else 0
     if n_mesh:
@@ -296,7 +313,7 @@ def make_scene(cfg: dict, seed: int | None = None) -> Scene:
         t, face = _nearest_hit(o, dd, boxes)
         nrm = np.zeros((t.shape[0], 3))
         if tris is not None:
-            tt, ti = _tri_nearest(o, dd, tris)
+            tt, ti = _tri_nearest(o, dd, tris, spheres)
             closer = tt < t
             t = np.where(closer, tt, t)
             face = np.where(closer, 5 + 6 * nb + ti // per_mesh, face)

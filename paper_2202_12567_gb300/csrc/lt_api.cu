@@ -99,6 +99,7 @@ extern "C" lt_status lt_destroy(lt_ctx* ctx) {
     cudaFree(ctx->d_boxes);
     cudaFree(ctx->d_cell_off);
     cudaFree(ctx->d_cell_box);
+    cudaFree(ctx->d_mesh);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -230,7 +231,15 @@ extern "C" lt_status lt_scene_upload(lt_ctx* ctx, const float* boxes, int64_t nb
                                         cudaMemcpyHostToDevice));
         }
     }
+    // a new scene has no triangles until lt_mesh_upload
+    cudaFree(ctx->d_mesh);
+    ctx->d_mesh = nullptr;
     Grid& g = ctx->grid;
+    g.nt = 0;
+    g.tri = nullptr;
+    g.bvh_aabb = nullptr;
+    g.bvh_child = nullptr;
+    g.bvh_tri = nullptr;
     g.box = ctx->d_boxes;
     g.cell_off = ctx->d_cell_off;
     g.cell_box = ctx->d_cell_box;

@@ -85,6 +85,13 @@ struct Grid {
     float lo[3];
     float cell[3];
     float inv_cell[3];
+    // triangle occluders (lt_mesh_upload): a linear BVH over nt triangles, internal
+    // nodes 0..nt-2 (root 0), leaf j = node nt-1+j holding triangle bvh_tri[j]
+    const float4* tri;       // [nt][3] v0, e1 = v1 - v0, e2 = v2 - v0 (w unused)
+    const float* bvh_aabb;   // [2nt-1][6] lo xyz, hi xyz
+    const int32_t* bvh_child;// [nt-1][2]
+    const int32_t* bvh_tri;  // [nt]
+    int nt;
 };
 
 // Closed-box slab test of o + t D over t in [kTMin, kTMax].
@@ -124,11 +131,10 @@ struct WorkCount {
     int boxes = 0;
 };
 
-// Any-hit test of the segment o -> e (t in (kTMin, kTMax)) by a 3-D DDA walk.
-// The walk is bounded by the number of cells a straight segment can cross.
+// Any-hit test of the segment o -> e (t in (kTMin, kTMax)) against the boxes by a 3-D
+// DDA walk.  The walk is bounded by the number of cells a straight segment can cross.
 template <bool COUNT = false>
-__device__ inline bool seg_blocked(const Grid& g, float3 o, float3 e, WorkCount* wc = nullptr) {
-    if (g.nb == 0) return false;
+__device__ inline bool grid_blocked(const Grid& g, float3 o, float3 e, WorkCount* wc = nullptr) {
     const float3 D = e - o;
     const int par = (D.x == 0.f ? 1 : 0) | (D.y == 0.f ? 2 : 0) | (D.z == 0.f ? 4 : 0);
     const float3 inv = make_float3((par & 1) ? 0.f : 1.f / D.x, (par & 2) ? 0.f : 1.f / D.y,
@@ -188,6 +194,69 @@ __device__ inline bool seg_blocked(const Grid& g, float3 o, float3 e, WorkCount*
         tn[a] += td[a];
     }
     return false;
+}
+
+// Closed triangle (v0, v0 + e1, v0 + e2) against o + t D, t in (kTMin, kTMax)
+// (Moller-Trumbore; a segment in the triangle's plane does not hit).
+__device__ __forceinline__ bool tri_hit(const float4* __restrict__ t3, float3 o, float3 D) {
+    const float4 a = t3[0], b = t3[1], c = t3[2];
+    const float3 v0 = make_float3(a.x, a.y, a.z), e1 = make_float3(b.x, b.y, b.z), e2 = make_float3(c.x, c.y, c.z);
+    const float3 p = make_float3(D.y * e2.z - D.z * e2.y, D.z * e2.x - D.x * e2.z, D.x * e2.y - D.y * e2.x);
+    const float det = dot3(e1, p);
+    if (det == 0.f) return false;
+    const float inv = 1.f / det;
+    const float3 sv = o - v0;
+    const float u = dot3(sv, p) * inv;
+    if (u < 0.f || u > 1.f) return false;
+    const float3 q = make_float3(sv.y * e1.z - sv.z * e1.y, sv.z * e1.x - sv.x * e1.z, sv.x * e1.y - sv.y * e1.x);
+    const float v = dot3(D, q) * inv;
+    if (v < 0.f || u + v > 1.f) return false;
+    const float t = dot3(e2, q) * inv;
+    return t > kTMin && t < kTMax;
+}
+
+// Any-hit test of the segment against the triangles: depth-first walk of the BVH
+// with an explicit stack.  The tree's keys are 64-bit and distinct, so it is at
+// most 64 levels deep and the stack (one entry pushed per level) cannot overflow;
+// the walk visits each node at most once, which bounds the loop.
+__device__ inline bool bvh_blocked(const Grid& g, float3 o, float3 e) {
+    const float3 D = e - o;
+    const int par = (D.x == 0.f ? 1 : 0) | (D.y == 0.f ? 2 : 0) | (D.z == 0.f ? 4 : 0);
+    const float3 inv = make_float3((par & 1) ? 0.f : 1.f / D.x, (par & 2) ? 0.f : 1.f / D.y,
+                                   (par & 4) ? 0.f : 1.f / D.z);
+    const int nt = g.nt, nl = nt - 1;  // leaves start at node nl
+    if (!slab_hit(g.bvh_aabb, o, inv, par)) return false;
+    int stack[64];
+    int sp = 0;
+    int node = 0;
+    for (int it = 0; it < 2 * nt; ++it) {
+        if (node >= nl) {  // leaf
+            if (tri_hit(g.tri + 3 * g.bvh_tri[node - nl], o, D)) return true;
+            if (sp == 0) break;
+            node = stack[--sp];
+            continue;
+        }
+        const int a = g.bvh_child[2 * node], b = g.bvh_child[2 * node + 1];
+        const bool ha = slab_hit(g.bvh_aabb + 6 * a, o, inv, par);
+        const bool hb = slab_hit(g.bvh_aabb + 6 * b, o, inv, par);
+        if (ha && hb) {
+            if (sp < 64) stack[sp++] = b;
+            node = a;
+        } else if (ha || hb) {
+            node = ha ? a : b;
+        } else {
+            if (sp == 0) break;
+            node = stack[--sp];
+        }
+    }
+    return false;
+}
+
+// Any-hit test of the segment o -> e against every occluder (boxes, then triangles).
+template <bool COUNT = false>
+__device__ inline bool seg_blocked(const Grid& g, float3 o, float3 e, WorkCount* wc = nullptr) {
+    if (g.nb > 0 && grid_blocked<COUNT>(g, o, e, wc)) return true;
+    return g.nt > 0 && bvh_blocked(g, o, e);
 }
 
 // ----------------------------------------------------------------- entry model
@@ -378,6 +447,7 @@ struct lt_ctx {
     float* d_boxes = nullptr;
     int32_t* d_cell_off = nullptr;
     int32_t* d_cell_box = nullptr;
+    void* d_mesh = nullptr;      // triangles and their BVH (lt_mesh_upload), one allocation
     ltk::Grid grid{};
     // scratch
     void* scr[SCR_NSLOTS] = {};

@@ -363,6 +363,75 @@ bool tree_ok(const lt_tree* t) {
     return t && t->n >= 1 && t->order && t->child && t->parent && t->range && t->rep && t->I && t->B && t->aabb;
 }
 
+// ------------------------------------------------------------------ triangle BVH
+// Linear BVH over triangles (the paper casts its shadow rays through a BVH, Sec. 6):
+// Morton codes of the centroids in the centroids' box, sorted with the triangle index
+// below them, the Karras topology, leaf boxes and a bottom-up refit.
+__global__ void k_tri_prep(const float* __restrict__ tris, int64_t nt, float4* __restrict__ cen,
+                           float4* __restrict__ rec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* t = tris + 9 * i;
+        const float3 a = make_float3(t[0], t[1], t[2]), b = make_float3(t[3], t[4], t[5]),
+                     c = make_float3(t[6], t[7], t[8]);
+        cen[i] = make_float4((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
+                             (a.z + b.z + c.z) * (1.f / 3.f), 0.f);
+        rec[3 * i] = make_float4(a.x, a.y, a.z, 0.f);
+        rec[3 * i + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, 0.f);
+        rec[3 * i + 2] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, 0.f);
+    }
+}
+
+__global__ void k_tri_keys(const float4* __restrict__ cen, int64_t nt, const float* __restrict__ box, int64_t npad,
+                           unsigned long long* keys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i >= nt) {
+            keys[i] = ~0ull;
+            continue;
+        }
+        const float4 c = cen[i];
+        keys[i] = ((unsigned long long)morton3(make_float3(c.x, c.y, c.z), box, box + 3) << 32) |
+                  (unsigned long long)i;
+    }
+}
+
+__global__ void k_bvh_leaves(const unsigned long long* __restrict__ keys, const float* __restrict__ tris, int64_t nt,
+                             int32_t* __restrict__ leaf_tri, float* __restrict__ aabb, int32_t* __restrict__ parent,
+                             int32_t* __restrict__ flags) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nt; j += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(keys[j] & 0xffffffffu);
+        leaf_tri[j] = t;
+        const float* v = tris + 9 * (int64_t)t;
+        float* bb = aabb + 6 * (nt - 1 + j);
+        for (int a = 0; a < 3; ++a) {
+            bb[a] = fminf(v[a], fminf(v[3 + a], v[6 + a]));
+            bb[3 + a] = fmaxf(v[a], fmaxf(v[3 + a], v[6 + a]));
+        }
+        if (j < nt - 1) flags[j] = 0;
+    }
+    if (nt == 1 && blockIdx.x == 0 && threadIdx.x == 0) parent[0] = -1;
+}
+
+// bottom-up boxes: the second thread to reach a node combines its children
+__global__ void k_bvh_up(int64_t nt, const int32_t* __restrict__ child, const int32_t* __restrict__ parent,
+                         float* aabb, int32_t* flags) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nt; j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t node = nt - 1 + j;
+        for (int guard = 0; guard < 128 && node > 0; ++guard) {
+            const int p = parent[node];
+            __threadfence();
+            if (atomicAdd(&flags[p], 1) == 0) break;
+            __threadfence();
+            const int a = child[2 * p], b = child[2 * p + 1];
+            for (int q = 0; q < 3; ++q) {
+                aabb[6 * p + q] = fminf(*(volatile float*)&aabb[6 * a + q], *(volatile float*)&aabb[6 * b + q]);
+                aabb[6 * p + 3 + q] =
+                    fmaxf(*(volatile float*)&aabb[6 * a + 3 + q], *(volatile float*)&aabb[6 * b + 3 + q]);
+            }
+            node = p;
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ tree
@@ -610,5 +679,86 @@ extern "C" lt_status lt_make_slices(lt_ctx* ctx, const float* pts, int64_t m, in
     for (int s = 0; s < S; ++s) off[s + 1] = off[s] + hc[s];
     LT_CUDA(ctx, cudaMemcpyAsync(slice_off, off.data(), (S + 1) * 4, cudaMemcpyHostToDevice, ctx->stream));
     LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LT_OK;
+}
+
+extern "C" lt_status lt_mesh_upload(lt_ctx* ctx, const float* tris, int64_t nt) {
+    if (!ctx || nt < 0 || (nt > 0 && !tris) || nt > (1 << 26))
+        return lt_fail(ctx, LT_EINVAL, "lt_mesh_upload: bad arguments");
+    if (ctx->graphs > 0)
+        return lt_fail(ctx, LT_EINVAL, "lt_mesh_upload: live frame graphs reference the current scene");
+    if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_mesh_upload: upload the boxes first");
+    cudaSetDevice(ctx->device);
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->d_mesh);
+    ctx->d_mesh = nullptr;
+    Grid& g = ctx->grid;
+    g.nt = 0;
+    g.tri = nullptr;
+    g.bvh_aabb = nullptr;
+    g.bvh_child = nullptr;
+    g.bvh_tri = nullptr;
+    if (nt == 0) return LT_OK;
+    const int64_t nn = 2 * nt - 1;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_rec = up((size_t)nt * 48), b_aabb = up((size_t)nn * 24), b_child = up((size_t)nn * 8),
+                 b_par = up((size_t)nn * 4), b_range = up((size_t)nn * 8), b_leaf = up((size_t)nt * 4);
+    char* m = nullptr;
+    LT_CUDA(ctx, cudaMalloc(&m, b_rec + b_aabb + b_child + b_par + b_range + b_leaf));
+    ctx->d_mesh = m;
+    float4* rec = (float4*)m;
+    float* aabb = (float*)(m + b_rec);
+    int32_t* child = (int32_t*)(m + b_rec + b_aabb);
+    int32_t* parent = (int32_t*)(m + b_rec + b_aabb + b_child);
+    int32_t* range = (int32_t*)(m + b_rec + b_aabb + b_child + b_par);
+    int32_t* leaf = (int32_t*)(m + b_rec + b_aabb + b_child + b_par + b_range);
+    const int64_t npad = next_pow2(nt);
+    lt_status st;
+    char* p = (char*)lt_scratch(ctx, SCR_SORT, (size_t)npad * 8 + (size_t)nt * 4 + (size_t)nt * 16 + 1024, &st);
+    if (!p) return st;
+    unsigned long long* keys = (unsigned long long*)p;
+    int32_t* flags = (int32_t*)(p + npad * 8);
+    float4* cen = (float4*)(p + up(npad * 8 + (size_t)nt * 4));
+    float* box = (float*)lt_scratch(ctx, SCR_MISC, 64, &st);
+    if (!box) return st;
+    const int blocks = (int)std::min<int64_t>((npad + 255) / 256, 16 * (int64_t)ctx->num_sms);
+    k_tri_prep<<<blocks, 256, 0, ctx->stream>>>(tris, nt, cen, rec);
+    LT_LAUNCH_CHECK(ctx, "k_tri_prep");
+    k_bbox<<<1, 1024, 0, ctx->stream>>>(cen, nt, box);
+    LT_LAUNCH_CHECK(ctx, "k_bbox");
+    k_tri_keys<<<blocks, 256, 0, ctx->stream>>>(cen, nt, box, npad, keys);
+    LT_LAUNCH_CHECK(ctx, "k_tri_keys");
+    if ((st = bitonic_sort(ctx, keys, npad)) != LT_OK) return st;
+    lt_tree view{};
+    view.n = nt;
+    view.child = child;
+    view.parent = parent;
+    view.range = range;
+    k_karras<<<blocks, 256, 0, ctx->stream>>>(keys, nt, view);
+    LT_LAUNCH_CHECK(ctx, "k_karras");
+    k_bvh_leaves<<<blocks, 256, 0, ctx->stream>>>(keys, tris, nt, leaf, aabb, parent, flags);
+    LT_LAUNCH_CHECK(ctx, "k_bvh_leaves");
+    if (nt > 1) {
+        LT_CUDA(ctx, cudaMemsetAsync(parent, 0xff, sizeof(int32_t), ctx->stream));  // the root
+        k_bvh_up<<<blocks, 256, 0, ctx->stream>>>(nt, child, parent, aabb, flags);
+        LT_LAUNCH_CHECK(ctx, "k_bvh_up");
+    }
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    g.nt = (int)nt;
+    g.tri = rec;
+    g.bvh_aabb = aabb;
+    g.bvh_child = child;
+    g.bvh_tri = leaf;
+    return LT_OK;
+}
+
+extern "C" lt_status lt_mesh_bvh(const lt_ctx* ctx, float* aabb, int32_t* child, int32_t* leaf_tri) {
+    if (!ctx || ctx->grid.nt < 1 || !aabb || !child || !leaf_tri) return LT_EINVAL;
+    const Grid& g = ctx->grid;
+    const int64_t nt = g.nt, nn = 2 * nt - 1;
+    if (cudaMemcpy(aabb, g.bvh_aabb, (size_t)nn * 24, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(child, g.bvh_child, (size_t)(nt - 1) * 8, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(leaf_tri, g.bvh_tri, (size_t)nt * 4, cudaMemcpyDeviceToDevice) != cudaSuccess)
+        return LT_ECUDA;
     return LT_OK;
 }

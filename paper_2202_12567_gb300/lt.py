@@ -106,6 +106,8 @@ _SIGS = {
                            ctypes.POINTER(lt_factors)]),
     "lt_complete_adm": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _f32, _u64,
                                ctypes.POINTER(lt_factors)]),
+    "lt_mesh_upload": (_i32, [_p, _p, _i64]),
+    "lt_mesh_bvh": (_i32, [_p, _p, _p, _p]),
     "lt_split_slice_count": (_i32, [_i64, _i32]),
     "lt_make_slices_split": (_i32, [_p, _p, _i64, _i32, _f32, _p, _p]),
     "lt_rgb_setup": (_i32, [_p, ctypes.POINTER(lt_frame), _p, _p, _p, ctypes.POINTER(lt_rgb)]),
@@ -483,6 +485,21 @@ def lt_complete_adm(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters
     ctx._check("lt_complete_adm", ctx.lib.lt_complete_adm(ctx.h, ctypes.byref(frame.struct()),
                                                           ctypes.byref(smp.struct()), iters, alpha_rel, gamma, seed,
                                                           ctypes.byref(uv.struct())))
+
+
+def lt_mesh_upload(ctx: Context, tris):
+    """tris: device float32 [nt, 9] (or [nt, 3, 3]); nt = 0 clears the triangles."""
+    t = tris.reshape(-1, 9).contiguous() if tris is not None and tris.numel() else None
+    ctx._check("lt_mesh_upload", ctx.lib.lt_mesh_upload(ctx.h, _ptr(t), 0 if t is None else t.shape[0]))
+    ctx._mesh = t  # the caller's buffer is only read during the call
+
+
+def lt_mesh_bvh(ctx: Context, nt: int, device):
+    aabb = torch.empty((2 * nt - 1, 6), dtype=torch.float32, device=device)
+    child = torch.empty((max(nt - 1, 1), 2), dtype=torch.int32, device=device)
+    leaf = torch.empty(nt, dtype=torch.int32, device=device)
+    ctx._check("lt_mesh_bvh", ctx.lib.lt_mesh_bvh(ctx.h, _ptr(aabb), _ptr(child), _ptr(leaf)))
+    return aabb, child[:nt - 1], leaf
 
 
 def lt_make_slices_split(ctx: Context, pts, target: int, normal_weight: float):

@@ -35,6 +35,9 @@ class Renderer:
         self.vpls = torch.from_numpy(np.ascontiguousarray(scene.vpls)).to(self.dev)
         self.boxes = torch.from_numpy(np.ascontiguousarray(scene.boxes)).to(self.dev).reshape(-1, 6)
         lt.lt_scene_upload(self.ctx, self.boxes)
+        if getattr(scene, "tris", None) is not None:  # triangle occluders of a mesh scene
+            self.tris = torch.from_numpy(np.ascontiguousarray(scene.tris, dtype=np.float32)).to(self.dev)
+            lt.lt_mesh_upload(self.ctx, self.tris)
         self.frame = None
 
     # ---------------------------------------------------------------- setup (a0)

@@ -45,7 +45,7 @@ def test_header_declares_the_entry_points():
     names = declared()
     assert len(names) >= 20, names
     for must in ("lt_create", "lt_sample_pass1", "lt_sample_pass2", "lt_eval_entries", "lt_complete",
-                 "lt_render", "lt_eval_entries_noalloc", "lt_complete_adm", "lt_rgb_setup", "lt_expand_rgb", "lt_make_slices_split", "lt_split_slice_count", "lt_sample_pass1_target"):
+                 "lt_render", "lt_eval_entries_noalloc", "lt_complete_adm", "lt_rgb_setup", "lt_expand_rgb", "lt_make_slices_split", "lt_split_slice_count", "lt_sample_pass1_target", "lt_mesh_upload", "lt_mesh_bvh"):
         assert must in names
 
 
