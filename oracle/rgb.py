@@ -106,17 +106,22 @@ def render_stacked(factors, row_perm, slice_off, m: int) -> np.ndarray:
     return img
 
 
-def render_frame(scene, cfg, st, seed=None):
+def render_frame(scene, cfg, st, seed=None, slices=None):
     """Steps 3-5 in colour: scalar sampling per slice, RGB values of the sampled pairs,
-    stacked completion, RGB image [m, 3].  Returns (image, per-slice (rows, cols,
-    col_node, vals_rgb))."""
+    stacked completion, RGB image [m, 3] (only the listed slices when given, the rest
+    black).  Returns (image, per-slice (rows, cols, col_node, vals_rgb))."""
     seed = cfg["frame_seed"] if seed is None else seed
     tree, forest, pts_s = st["tree"], st["forest"], st["pts_s"]
     S = len(st["slice_off"]) - 1
+    todo = set(range(S) if slices is None else slices)
     factors, omega = [], []
     for s in range(S):
         a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
         m_s = b - a
+        if s not in todo:
+            factors.append((np.zeros((3 * m_s, 1)), np.zeros((0, 1))))
+            omega.append(None)
+            continue
         p1 = pass1.coarsen_slice(tree, forest, pts_s, scene.vpls, scene.occluders, s, a, m_s, cfg["rate1"], cfg["tau"],
                                  seed, cfg["d_min"], target=pipeline.target_cut(cfg))
         n_s = p1.col_node.size

@@ -46,24 +46,26 @@ def rows_of(slice_off, slices) -> np.ndarray:
 
 
 def gather_image(pixels: torch.Tensor, values: torch.Tensor, m: int, dst: int = 0, group=None):
-    """Every rank holds values at pixel indices; rank `dst` returns the full image
-    [m] (other ranks None).  Blocks of different sizes are padded to the largest."""
+    """Every rank holds values [k, ...] at pixel indices [k]; rank `dst` returns the
+    full image [m, ...] (other ranks None), e.g. [m] or [m, 3] for colour.  Blocks of
+    different sizes are padded to the largest."""
     world = dist.get_world_size(group)
+    tail = tuple(values.shape[1:])
     n = torch.tensor([pixels.numel()], dtype=torch.int64)
     sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
     dist.all_gather(sizes, n, group=group)
     cap = int(max(int(x.item()) for x in sizes))
     pad_p = torch.full((cap,), -1, dtype=torch.int64)
-    pad_v = torch.zeros(cap, dtype=values.dtype)
+    pad_v = torch.zeros((cap,) + tail, dtype=values.dtype)
     pad_p[:pixels.numel()] = pixels.to(torch.int64).cpu()
-    pad_v[:values.numel()] = values.cpu()
+    pad_v[:pixels.numel()] = values.cpu()
     all_p = [torch.empty(cap, dtype=torch.int64) for _ in range(world)]
-    all_v = [torch.empty(cap, dtype=values.dtype) for _ in range(world)]
+    all_v = [torch.empty((cap,) + tail, dtype=values.dtype) for _ in range(world)]
     dist.all_gather(all_p, pad_p, group=group)
     dist.all_gather(all_v, pad_v, group=group)
     if dist.get_rank(group) != dst:
         return None
-    img = torch.zeros(m, dtype=values.dtype)
+    img = torch.zeros((m,) + tail, dtype=values.dtype)
     seen = torch.zeros(m, dtype=torch.bool)
     for p, v, k in zip(all_p, all_v, sizes):
         k = int(k.item())

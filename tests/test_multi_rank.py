@@ -82,3 +82,38 @@ def test_two_ranks_render_the_single_process_frame(tmp_path):
     got = np.load(out)
     assert np.array_equal(got, want)
     assert float(open(out + ".t").read()) == 11.0
+
+
+def _rank_main_rgb(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from ltinputs import get_config, make_scene
+        from oracle import pipeline, rgb
+        cfg = get_config("room64_vpl1k_2box", width=32, height=32, n_vpl=256, max_cut=64, n_slices=6, rgb=True)
+        sc = make_scene(cfg)
+        st = pipeline.setup(sc, cfg)
+        mine = shard.lpt_partition(shard.slice_costs(st["slice_off"], C=len(st["cut"])), world)[rank]
+        img_part, _ = rgb.render_frame(sc, cfg, st, slices=mine)
+        rows = shard.rows_of(st["slice_off"], mine)
+        pix = torch.from_numpy(st["row_perm"][rows].astype(np.int64))
+        vals = torch.from_numpy(img_part[pix.numpy()])
+        img = shard.gather_image(pix, vals, sc.m)
+        if rank == 0:
+            np.save(out, img.numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.slow
+def test_two_ranks_gather_a_colour_frame(tmp_path):
+    """Colour pixel blocks [k, 3] gathered over two gloo ranks give the whole image."""
+    from ltinputs import get_config, make_scene
+    from oracle import pipeline, rgb
+    out = str(tmp_path / "rgb.npy")
+    mp.start_processes(_rank_main_rgb, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    cfg = get_config("room64_vpl1k_2box", width=32, height=32, n_vpl=256, max_cut=64, n_slices=6, rgb=True)
+    sc = make_scene(cfg)
+    want, _ = rgb.render_frame(sc, cfg, pipeline.setup(sc, cfg))
+    got = np.load(out)
+    assert got.shape == (sc.m, 3) and np.array_equal(got, want)
