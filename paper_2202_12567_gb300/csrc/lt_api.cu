@@ -231,7 +231,9 @@ extern "C" lt_status lt_scene_upload(lt_ctx* ctx, const float* boxes, int64_t nb
                                         cudaMemcpyHostToDevice));
         }
     }
-    // a new scene has no triangles until lt_mesh_upload
+    // a new scene has no triangles until lt_mesh_upload (no kernel of the stream may
+    // still read the old ones)
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     cudaFree(ctx->d_mesh);
     ctx->d_mesh = nullptr;
     Grid& g = ctx->grid;

@@ -754,6 +754,7 @@ extern "C" lt_status lt_mesh_upload(lt_ctx* ctx, const float* tris, int64_t nt) 
 
 extern "C" lt_status lt_mesh_bvh(const lt_ctx* ctx, float* aabb, int32_t* child, int32_t* leaf_tri) {
     if (!ctx || ctx->grid.nt < 1 || !aabb || !child || !leaf_tri) return LT_EINVAL;
+    cudaSetDevice(ctx->device);
     const Grid& g = ctx->grid;
     const int64_t nt = g.nt, nn = 2 * nt - 1;
     if (cudaMemcpy(aabb, g.bvh_aabb, (size_t)nn * 24, cudaMemcpyDeviceToDevice) != cudaSuccess ||
