@@ -9,6 +9,7 @@ import re
 import shutil
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -93,3 +94,19 @@ def test_status_strings_without_a_device(libpath):
     lib.lt_create.restype = ctypes.c_int32
     lib.lt_create.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     assert lib.lt_create(None, 0, None) == 1  # null output handle: LT_EINVAL, nothing touched
+
+
+def test_split_slice_count_is_host_only_and_matches_the_oracle(libpath):
+    """lt_split_slice_count plans the recursive split on the host (no device needed);
+    its slice count equals the oracle's leaf sizes for many (m, target)."""
+    from oracle import slices
+    lib = ctypes.CDLL(libpath)
+    f = lib.lt_split_slice_count
+    f.restype = ctypes.c_int32
+    f.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    rng = np.random.default_rng(0)
+    cases = [(1, 1), (7, 2), (1000, 100), (65536, 800), (262144, 800)]
+    cases += [(int(rng.integers(1, 200000)), int(rng.integers(1, 5000))) for _ in range(40)]
+    for m, target in cases:
+        assert f(m, target) == len(slices.split_sizes(m, target)), (m, target)
+    assert f(0, 10) == -1 and f(10, 0) == -1
