@@ -482,8 +482,16 @@ def run_ours(args):
 
     roof = als_roofline(lt, ctx, R, half_ms)
     roof_eval = eval_roofline(lt, ctx, R, stage_ms, clk)
-    colour = rgb_leg(args, local, flush)
-    meshes = mesh_leg(args, local, flush)
+    # the colour and mesh forms run on contexts of their own after the headline; a
+    # failure there is reported in the line instead of losing it
+    try:
+        colour = rgb_leg(args, local, flush)
+    except RuntimeError as e:
+        colour = dict(error=str(e))
+    try:
+        meshes = mesh_leg(args, local, flush)
+    except RuntimeError as e:
+        meshes = dict(error=str(e))
 
     line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
