@@ -110,3 +110,37 @@ def test_split_slice_count_is_host_only_and_matches_the_oracle(libpath):
     for m, target in cases:
         assert f(m, target) == len(slices.split_sizes(m, target)), (m, target)
     assert f(0, 10) == -1 and f(10, 0) == -1
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """Every struct the binding mirrors has the C size and field offsets (compiled
+    with the system C compiler against include/lt.h)."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    from paper_2202_12567_gb300 import lt
+    structs = {"lt_tree": lt.lt_tree, "lt_frame": lt.lt_frame, "lt_samples": lt.lt_samples,
+               "lt_factors": lt.lt_factors, "lt_rgb": lt.lt_rgb, "lt_params": lt.lt_params,
+               "lt_tuning": lt.lt_tuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lt.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([gcc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for row in out:
+        if not row:
+            continue
+        name, what, value = row.split()
+        cls = structs[name]
+        want = ctypes.sizeof(cls) if what == "size" else getattr(cls, what).offset
+        assert int(value) == want, (name, what, int(value), want)
+        seen += 1
+    assert seen == sum(1 + len(c._fields_) for c in structs.values())
