@@ -46,62 +46,140 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-slices", type=int, default=2, help="slices of the frame in the CPU sample")
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_sample(workload: str, n_slices_sample: int) -> dict:
-    """Time the CPU oracle on a bounded sample of one frame, in a fresh process with
-    single-threaded numpy, and scale to a whole frame by the rows processed."""
-    code = f"""
-import os, sys, time, json
-sys.path.insert(0, {ROOT!r})
-import numpy as np
-from ltinputs import get_config, make_scene
-from oracle import pipeline
-cfg = get_config({workload!r})
-sc = make_scene(cfg)
-st = pipeline.setup(sc, cfg)
-off = st["slice_off"]
-S = len(off) - 1
-pick = list(range(0, S, max(1, S // {n_slices_sample})))[:{n_slices_sample}]
-rows = int(sum(off[s + 1] - off[s] for s in pick))
-t0 = time.perf_counter()
-for s in pick:
-    pipeline.run_slice(st, sc, cfg, s, cfg["frame_seed"])
-dt = time.perf_counter() - t0
-print(json.dumps(dict(seconds=dt, rows=rows, m=int(sc.m), slices=pick)))
-"""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    ms_frame = r["seconds"] * 1e3 * r["m"] / r["rows"]
-    return dict(value=ms_frame, unit="ms/frame", cores=1, kind="oracle",
-                sample=f"slices {r['slices']} ({r['rows']} of {r['m']} rows) of one frame, "
-                       f"{r['seconds']:.1f} s of CPU time, scaled by rows")
+# The oracle runs slice by slice (slices are independent after setup), one slice per
+# process of a spawn pool over the host cores, each process single-threaded numpy.
+_ORACLE = {}
+
+
+def _oracle_init(sc, st, cfg):
+    _ORACLE.update(sc=sc, st=st, cfg=cfg)
+
+
+def _oracle_noop(_):
+    return os.getpid()
+
+
+def _oracle_slice(s, seed):
+    from oracle import pipeline
+    t0 = time.perf_counter()
+    pipeline.run_slice(_ORACLE["st"], _ORACLE["sc"], _ORACLE["cfg"], s, seed)
+    return s, time.perf_counter() - t0
+
+
+def _oracle_pool(sc, st, cfg, cores):
+    """A warmed spawn pool of `cores` single-threaded oracle processes."""
+    import multiprocessing
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                           "CUDA_VISIBLE_DEVICES")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+    try:
+        pool = multiprocessing.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(sc, st, cfg))
+        pool.map(_oracle_noop, range(4 * cores), chunksize=1)  # every worker started and initialised
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool
+
+
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def oracle_sample(workload: str, setup=None) -> dict:
+    """cpu_baseline: the CPU oracle on one wave of slices, one slice per host core,
+    the slices spread over the frame's size range, timed wall-clock; ms/frame =
+    wall x m / (rows of the wave).  `setup` = (cut, row_perm, slice_off) of the GPU's
+    setup, so the oracle skips its own (untimed either way)."""
+    import numpy as np
+    from ltinputs import get_config, make_scene
+    from oracle import pipeline
+    cfg = get_config(workload)
+    sc = make_scene(cfg)
+    if setup is None:
+        st = pipeline.setup(sc, cfg)
+    else:
+        cut, perm, off = setup
+        st = pipeline.setup(sc, cfg, cut=cut, slicing=(perm, off))
+    off = np.asarray(st["slice_off"])
+    sizes = np.diff(off)
+    S = sizes.size
+    cores = host_cores()
+    k = min(S, cores)
+    order = np.argsort(sizes, kind="stable")
+    pick = sorted({int(order[int(round(q * (S - 1)))]) for q in np.linspace(0.0, 1.0, k)})
+    pool = _oracle_pool(sc, st, cfg, cores)
+    try:
+        t0 = time.perf_counter()
+        res = pool.starmap(_oracle_slice, [(s, cfg["frame_seed"]) for s in pick], chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    rows = int(sizes[pick].sum())
+    cpu_s = sum(t for _, t in res)
+    ms_frame = wall * 1e3 * sc.m / rows
+    return dict(value=round(ms_frame, 1), unit="ms/frame", cores=cores, kind="oracle",
+                sample=f"{len(pick)} of {S} slices ({rows} of {sc.m} rows, sizes {int(sizes[pick].min())}-"
+                       f"{int(sizes[pick].max())}) run at once, one per process on {cores} host cores: "
+                       f"{wall:.1f} s wall, {cpu_s:.1f} s CPU; ms/frame = wall x m / rows of the sample; "
+                       f"setup (tree, cut, slices) not timed")
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands on the host cores.  Step k is
+    one slice (spread over the frame) run by one single-threaded process; the K steps
+    run concurrently on a spawn pool over the host cores.  A step's ms/frame is its
+    slice time scaled to the frame's rows on all cores, t_k x m / (m'_k x cores);
+    the line reports their median, and ms_per_step is the wall time of the whole
+    timed run divided by K."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    vals = []
-    for _ in range(args.warmup):
-        pass  # the oracle has nothing to warm up; warm-up steps are not repeated on the CPU
-    for _ in range(max(1, args.steps)):
-        vals.append(oracle_sample(args.workload, args.cpu_slices))
-        if sum(v["value"] for v in vals) > 0 and len(vals) >= 1 and args.steps > 1:
-            # one bounded sample per step would take minutes; one sample stands for all steps
-            break
-    v = vals[0]
-    line = dict(impl="reference", metric=METRIC, value=round(v["value"], 3), unit="ms/frame",
-                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup, ms_per_step=round(v["value"], 3),
+    import numpy as np
+    from ltinputs import get_config, make_scene
+    from oracle import pipeline
+    cfg = get_config(args.workload)
+    sc = make_scene(cfg)
+    t_setup = time.perf_counter()
+    st = pipeline.setup(sc, cfg)  # untimed: the frame metric excludes setup on both arms
+    t_setup = time.perf_counter() - t_setup
+    sizes = np.diff(np.asarray(st["slice_off"]))
+    S = sizes.size
+    K = max(1, args.steps)
+    cores = host_cores()
+    pick = [int(k * S // K) % S for k in range(K)]
+    pool = _oracle_pool(sc, st, cfg, min(cores, K))
+    try:
+        t0 = time.perf_counter()
+        res = pool.starmap(_oracle_slice, [(s, cfg["frame_seed"]) for s in pick], chunksize=1)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    per = [t * 1e3 * sc.m / (int(sizes[s]) * cores) for s, t in res]
+    value = float(np.median(per))
+    sample = (f"{K} steps, step k = slice {pick[0]}, {pick[1] if K > 1 else ''}... (one slice each, "
+              f"{int(sizes[pick].min())}-{int(sizes[pick].max())} rows) run concurrently on {min(cores, K)} "
+              f"single-threaded processes of {cores} host cores; step ms/frame = slice time x m / (rows x "
+              f"{cores} cores), median over steps; timed run {wall:.1f} s wall; oracle setup {t_setup:.1f} s "
+              f"untimed; warm-up steps: none run (no caches or compilation on the CPU path)")
+    line = dict(impl="reference", metric=METRIC, value=round(value, 1), unit="ms/frame",
+                n_gpus=args.gpus, steps=K, warmup=args.warmup, ms_per_step=round(wall * 1e3 / K, 1),
                 higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=args.workload), cpu_baseline=v,
-                e2e=dict(value=round(v["value"], 3), unit="ms/frame", h2d_bytes_per_step=0,
-                         d2h_bytes_per_step=0))
+                config=dict(workload=args.workload),
+                cpu_baseline=dict(value=round(value, 1), unit="ms/frame", cores=cores, kind="oracle",
+                                  sample=sample),
+                e2e=dict(value=round(value, 1), unit="ms/frame", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
 
@@ -151,28 +229,39 @@ class ClockSampler:
 OPS_ENTRY, OPS_RAY, OPS_CELL, OPS_BOX = 40, 40, 6, 24
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu
+# capture of each kernel on room256_vpl16k_2box; the summaries under profiles/ give
+# the commands.  A kernel changed since its capture has no entry here.
+MEASURED_TRAFFIC = {
+    "k_render": 7_060_480,
+}
 
-def eval_roofline(lt, ctx, R, stage_ms, clk):
+
+def fp32_peak(clk) -> dict:
+    """FP32 peak from the unit counts (152 SMs x 128 lanes x 2 flops per FMA) at the
+    maximum SM clock and at the median SM clock sampled during the timed region."""
+    at_max = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    mhz = clk.get("sm_mhz") or MAX_SM_MHZ
+    return dict(peak=round(at_max, 2), peak_at_sampled_clock=round(SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12, 2),
+                peak_source=f"152 SMs x 128 FP32 lanes x 2 (FMA) x {MAX_SM_MHZ:.0f} MHz max SM clock (derived; "
+                            f"no measured FP32 peak); at the sampled median {mhz:.0f} MHz in peak_at_sampled_clock")
+
+
+def eval_roofline(lt, ctx, R, eval_ms, clk):
     """ALU roofline of the entry-evaluation kernel (the shadow-ray kernel)."""
     st = lt.lt_eval_stats(ctx, R.frame, R.smp, R.cfg["d_min"])
     ops = OPS_ENTRY * st["entries"] + OPS_RAY * st["rays"] + OPS_CELL * st["cells"] + OPS_BOX * st["boxes"]
-    secs = stage_ms[2] * 1e-3
+    secs = eval_ms * 1e-3
     achieved = ops / secs / 1e12 if secs > 0 else 0.0
-    peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    return dict(bound="alu", kernel="k_eval_entries", achieved=round(achieved, 3), peak=round(peak, 2),
-                unit="TFLOP/s", frac=round(achieved / peak, 4), traffic=None,
-                peak_source="152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max SM clock",
+    pk = fp32_peak(clk)
+    return dict(bound="alu", kernel="k_eval_entries", achieved=round(achieved, 3), unit="TFLOP/s",
+                frac=round(achieved / pk["peak"], 4), traffic=MEASURED_TRAFFIC.get("k_eval_entries"),
+                launch_ms=round(eval_ms, 4), **pk,
                 work=dict(entries=st["entries"], rays=st["rays"], cells=st["cells"], boxes=st["boxes"],
                           ops_per_launch=int(ops)))
 
 
-# DRAM bytes per ALS half-step launch on this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture of k_als_line<16>: U-step 40,989,952,
-# V-step 42,801,408; their mean)
-ALS_TRAFFIC_BYTES = 41_895_680
-
-
-def als_roofline(lt, ctx, R, half_ms):
+def als_roofline(lt, ctx, R, half_ms, clk):
     """FP32 roofline of the lane-group ALS half-step (k_als_line): per observed entry
     r(r+1)/2 + r FMAs (Gram lower triangle and right-hand side), per line a Cholesky
     (r^3/3 flops) and two triangular solves (2 r^2 flops)."""
@@ -181,13 +270,43 @@ def als_roofline(lt, ctx, R, half_ms):
     lines = (R.frame.m + int(R.smp.ncol.sum())) / 2.0
     flops = 2.0 * E * (r * (r + 1) / 2 + r) + lines * (r ** 3 / 3.0 + 2.0 * r * r)
     achieved = flops / (half_ms * 1e-3) / 1e12
-    peak = SMS * FP32_LANES * 2 * MAX_SM_MHZ * 1e6 / 1e12
-    return dict(bound="alu", kernel="k_als_line (ALS half-step)", achieved=round(achieved, 3), peak=round(peak, 2),
-                unit="TFLOP/s", frac=round(achieved / peak, 4),
-                traffic=ALS_TRAFFIC_BYTES if R.cfg["rank"] == 16 else None,
-                peak_source="152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max SM clock (derived)",
-                launch_ms=round(half_ms, 4),
+    pk = fp32_peak(clk)
+    return dict(bound="alu", kernel="k_als_line (ALS half-step)", achieved=round(achieved, 3), unit="TFLOP/s",
+                frac=round(achieved / pk["peak"], 4),
+                traffic=MEASURED_TRAFFIC.get("k_als_line") if R.cfg["rank"] == 16 else None,
+                launch_ms=round(half_ms, 4), **pk,
                 work=dict(entries=E, lines_per_half_step=lines, flops_per_launch=int(flops)))
+
+
+def render_roofline(R, render_ms, peaks):
+    """HBM roofline of the render kernel: it reads U (4 r m bytes), V of every slice's
+    columns (4 r sum n'), the row permutation (4 m) and writes the image (4 m)."""
+    r = R.uv.r
+    byts = 4 * r * (R.frame.m + int(R.smp.ncol.sum())) + 8 * R.frame.m
+    achieved = byts / (render_ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return dict(bound="hbm", kernel="k_render", achieved=round(achieved, 1), peak=peak, unit="GB/s",
+                frac=round(achieved / peak, 4), traffic=MEASURED_TRAFFIC.get("k_render"),
+                launch_ms=round(render_ms, 4), bytes_per_launch=int(byts),
+                peak_source="measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks
+                else "fallback 6.8 TB/s")
+
+
+def timed(fn, reps, flush=None):
+    """Median device time (ms) of fn() on the current stream, L2 flushed before each."""
+    import torch
+    xs = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        xs.append(a.elapsed_time(b))
+    return statistics.median(xs)
 
 
 # ------------------------------------------------------------------ GPU leg
@@ -230,7 +349,7 @@ def rgb_leg(args, device: int, flush) -> dict | None:
     rel = float(torch.linalg.norm(img - ref) / torch.linalg.norm(ref))
     out = dict(workload=f"{name}: RGB face albedos, light colour {tuple(cfg['light_rgb'])}, 3 channels stacked "
                         f"as rows of each slice (3m' x n', one V)",
-               ms_per_frame=round(statistics.mean(ts), 3), stacked_completion_ms=round(statistics.mean(tc), 3),
+               ms_per_frame=round(statistics.median(ts), 3), stacked_completion_ms=round(statistics.median(tc), 3),
                rel_rmse_vs_rgb_bruteforce=round(rel, 5), pixel_entries=int(R.smp.cnt.sum().item()),
                stacked_entries=int(R.rgb.cnt.sum().item()))
     lt.lt_sync(R.ctx)
@@ -270,7 +389,7 @@ def mesh_leg(args, device: int, flush) -> dict | None:
     lt.lt_sync(R.ctx)
     return dict(workload=f"{name}: {sc.tris.shape[0]} triangles ({cfg['n_meshes']} icospheres) and "
                          f"{sc.nb} boxes as occluders",
-                ms_per_frame=round(statistics.mean(ts), 3), rel_rmse_vs_bruteforce=round(rel, 5),
+                ms_per_frame=round(statistics.median(ts), 3), rel_rmse_vs_bruteforce=round(rel, 5),
                 rays_per_pixel=round(float(R.rays()) / R.frame.m, 2))
 
 
@@ -374,30 +493,32 @@ def run_ours(args):
     launches = lt.lt_launch_count(ctx) - launches0
     lt.lt_sync(ctx)
     total_ms = float(sum(per))
+    med_ms = float(statistics.median(per))
     if world > 1:
         from paper_2202_12567_gb300 import shard
         total_ms = shard.max_over_ranks(total_ms, device=dev)
+        med_ms = shard.max_over_ranks(med_ms, device=dev)
         dist.barrier()
-    ms_frame = total_ms / (args.steps * world)
+    ms_frame = med_ms / world  # median replay, max over ranks; every rank renders its own frames
     img = R.img.clone()
     # the same graph with the paper's pdf g (seeds as above: the same pass-1 draws)
     per_g = replay(graph_g, 1000)
     img_g = R.img.clone()
-    g_graph_ms = statistics.mean(per_g)
+    g_graph_ms = statistics.median(per_g)
 
     # the plain form (the same calls one by one, with the two size read-backs),
     # with events between the stages for the breakdown
     plain = []
-    stage_ms = np.zeros(5)
+    stages = []
     for k in range(args.steps):
         flush.zero_()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         frame(1000 + k, evs)
         torch.cuda.synchronize()
         plain.append(evs[0].elapsed_time(evs[5]))
-        stage_ms += np.array([evs[j].elapsed_time(evs[j + 1]) for j in range(5)])
-    stage_ms /= args.steps
-    plain_ms = statistics.mean(plain)
+        stages.append([evs[j].elapsed_time(evs[j + 1]) for j in range(5)])
+    stage_ms = np.median(np.array(stages), axis=0)
+    plain_ms = statistics.median(plain)
     same_as_graph = bool(torch.equal(R.img, img_g))
     # ALS half-step on the launching stream: complete at K sweeps minus at 0 sweeps
     c_ms = {}
@@ -476,12 +597,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         if k > 0:
             e2e.append(a.elapsed_time(b))
-    e2e_ms = statistics.mean(e2e)
+    e2e_ms = statistics.median(e2e)
     h2d = sc.points.nbytes + sc.vpls.nbytes
     d2h = img_h.numel() * 4
 
-    roof = als_roofline(lt, ctx, R, half_ms)
-    roof_eval = eval_roofline(lt, ctx, R, stage_ms, clk)
+    roof = als_roofline(lt, ctx, R, half_ms, clk)
+    eval_ms = timed(lambda: lt.lt_eval_entries(ctx, R.frame, R.smp, cfg["d_min"]), max(5, args.steps // 2), flush)
+    roof_eval = eval_roofline(lt, ctx, R, eval_ms, clk)
+    render_ms = timed(lambda: lt.lt_render(ctx, R.frame, R.smp, R.uv, R.row_perm, img_als), max(5, args.steps // 2),
+                      flush)
+    roof_render = render_roofline(R, render_ms, peaks)
     # the colour and mesh forms run on contexts of their own after the headline; a
     # failure there is reported in the line instead of losing it
     try:
@@ -512,6 +637,7 @@ def run_ours(args):
                             plain_equals_graph_bitwise=same_as_graph,
                             tuning=dict(key=tune_key, values=tune_values, from_cache=tune_cached),
                             eval_roofline=roof_eval,
+                            render_roofline=roof_render,
                             adm_completion=adm,
                             rgb=colour,
                             mesh=meshes,
@@ -523,9 +649,12 @@ def run_ours(args):
                 gpu_launches=int(launches), clocks=clk, roofline=roof)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            line["cpu_baseline"] = oracle_sample(args.workload, args.cpu_slices)
+            line["cpu_baseline"] = oracle_sample(args.workload, setup=(R.frame.cut.cpu().numpy(),
+                                                                      R.row_perm.cpu().numpy(),
+                                                                      R.slice_off.cpu().numpy()))
         except Exception as e:  # report, do not hide
-            line["cpu_baseline"] = dict(value=None, unit="ms/frame", cores=1, kind="oracle", sample=f"failed: {e}")
+            line["cpu_baseline"] = dict(value=None, unit="ms/frame", cores=host_cores(), kind="oracle",
+                                        sample=f"failed: {e}")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

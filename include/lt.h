@@ -171,6 +171,13 @@ lt_status lt_build_global_cut(lt_ctx* ctx, const lt_tree* tree, const float* pts
                               const float* vpls, const int32_t* rows, int64_t nr, float eps,
                               int32_t max_cut, float growth, float d_min, int32_t* cut,
                               int32_t* cut_size_host);
+/* Errors of the nodes of a given cut, as one refinement round of
+ * lt_build_global_cut computes them (the same kernels and summation order):
+ * err[c] = max over the test rows x of bound(x, cut[c]) / estimate(x), infinite
+ * where the estimate is zero and the bound is not.  cut[C] and err[C] are device
+ * arrays.  Instrumentation for checking the refinement round by round. */
+lt_status lt_cut_errors(lt_ctx* ctx, const lt_tree* tree, const float* pts, int64_t m, const float* vpls,
+                        const int32_t* rows, int64_t nr, const int32_t* cut, int32_t C, float d_min, float* err);
 /* Forest of the cut (layout in lt_frame).  forest[(2C-1)*8], level_off[max_levels+2],
  * level_nodes[C-1]; *height_host receives H. */
 lt_status lt_cut_forest(lt_ctx* ctx, const lt_tree* tree, const int32_t* cut, int32_t C,
@@ -248,9 +255,16 @@ lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, const lt_sa
                         int64_t* stats_host);
 /* Masked ALS at rank r (uv->rank[s] per slice when given), `iters` sweeps (U-step
  * then V-step), ridge lam_rel trace(G)/r, V0 from Philox (k, j, slice, 3); float32
- * Cholesky with a float64 retry when min/max pivot^2 < 1e-6. */
+ * Cholesky with a float64 retry when min/max pivot^2 < 1e-6 (the retry forms the
+ * line's Gram again in float64 and solves it in float64). */
 lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
                       float lam_rel, uint64_t seed, lt_factors* uv);
+/* Lines (rows of U or columns of V, summed over every half-step) that the last
+ * lt_complete of the context solved in float64 because their float32 pivots failed
+ * the check above; their Gram is formed again in float64 from the float32 factors.
+ * Synchronises the context's stream.  0 before the first lt_complete.
+ * Instrumentation; the paper has no counterpart. */
+lt_status lt_complete_fp64_lines(lt_ctx* ctx, int64_t* count_host);
 /* Nonnegative completion of every slice by the alternating direction method of
  * App. A, `iters` iterations (X step, Y step, Z, U, V, Lambda, Pi in the appendix's
  * order) at rank r (uv->rank[s] per slice when given).  Readings: the Y step uses

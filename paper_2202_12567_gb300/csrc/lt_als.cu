@@ -708,16 +708,20 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
 // slice's factor rows staged in shared memory and accumulates the lower triangle of
 // G = sum x_j x_j^T and b = sum a_j x_j in registers (RP(RP+1)/2 + RP values),
 // adds the ridge lam_rel tr(G)/r, factors G by Cholesky in float32 and solves.
-// Lines whose pivots fail the check go to a queue that a float64 pass solves.
+// Lines whose pivots fail the check go to a queue; a second kernel forms their
+// Gram again in float64 (products of the float32 factors are exact in float64) and
+// solves it in float64, so an ill-conditioned line carries no float32 rounding.
 template <int RP>
 struct AlsQueue {
-    static constexpr int kVals = RP * (RP + 1) / 2 + RP;
     int32_t* count;     // [1] lines queued by this half-step
     int64_t* dst;       // [cap] output row offset (floats) of each queued line
-    float* gram;        // [cap][kVals] Gram lower triangle then right-hand side
+    int64_t* slot;      // [cap] first slot of the line's first lane stream in the sliced layout
+    int64_t* src;       // [cap] offset (floats) in the source factors of the slice's rows
+    int32_t* len;       // [cap] entries of the line
+    int32_t* grp;       // [cap] lanes G of the line (entry e is entry e / G of stream e % G)
+    int32_t* rank;      // [cap] rank of each queued line
     int64_t cap;
     int32_t* status;    // device status word (LT_ELIMIT when the queue overflows)
-    int32_t* rank;      // [cap] rank of each queued line
 };
 
 // Cholesky solve of (G + lam I) u = b in place (u returned in b); rows i >= r are
@@ -852,7 +856,8 @@ __device__ __forceinline__ void stream_gram(int nk, const uint2* __restrict__ id
 // lanes of the line, `slot` the first slot of its stream (task base + 4 lane).
 template <int RP>
 __device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int r, int R, bool rows_side,
-                                         const float* __restrict__ src, bool staged, const float4* stage4,
+                                         const float* __restrict__ src_base, const float* __restrict__ src,
+                                         bool staged, const float4* stage4,
                                          float* __restrict__ Fout, float lam_rel, const AlsQueue<RP>& q, int s,
                                          int line, int sub, int G, int64_t slot) {
     constexpr int NA = RP * (RP + 1) / 2;
@@ -894,26 +899,18 @@ __device__ __forceinline__ void als_line(const lt_frame& F, const Omega& om, int
             if (i < r) Fout[dst + i] = bb[i];
         return;
     }
-    // rare: queue the Gram (accumulated again by this lane over the G streams) for float64
+    // rare: queue the line for the float64 pass (k_als_retry)
     const int qs = atomicAdd(q.count, 1);
     if (qs >= q.cap) {
         latch(q.status, LT_ELIMIT);
         return;
     }
-#pragma unroll
-    for (int i = 0; i < NA; ++i) a[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) bb[i] = 0.f;
-    for (int u = 0; u < G; ++u)
-        stream_gram<RP>(u < len ? (len - u + G - 1) / G : 0, reinterpret_cast<const uint2*>(sidx + slot + 4 * u),
-                        reinterpret_cast<const float4*>(sval + slot + 4 * u), r, R, src, staged, stage4, a, bb);
     q.dst[qs] = dst;
+    q.slot[qs] = slot;
+    q.src[qs] = src - src_base;
+    q.len[qs] = len;
+    q.grp[qs] = G;
     q.rank[qs] = r;
-    float* gq = q.gram + (int64_t)qs * AlsQueue<RP>::kVals;
-#pragma unroll
-    for (int i = 0; i < NA; ++i) gq[i] = a[i];
-#pragma unroll
-    for (int i = 0; i < RP; ++i) gq[NA + i] = bb[i];
 }
 
 // stage the slice's source factor rows (nsrc rows of stride R, the first r values,
@@ -1040,33 +1037,91 @@ __global__ void __launch_bounds__(256, 1) k_als_line(lt_frame F, lt_samples smp,
             const int g = kClasses - 1 - k, G = 1 << g;
             const int li = cls[k] + (tk - cls[8 + k]) * (32 >> g) + (lane >> g);
             const bool live = li < cls[k + 1];
-            als_line<RP>(F, om, r, R, rows_side, src, staged, stage4, Fout, lam_rel, q, sl, live ? ord[li] : -1,
+            als_line<RP>(F, om, r, R, rows_side, Fin, src, staged, stage4, Fout, lam_rel, q, sl, live ? ord[li] : -1,
                          lane & (G - 1), G, base[sl] + tb[tk] + 4 * lane);
         }
         __syncthreads();  // the stage is reused by the next segment
     }
 }
 
-// float64 solve of the queued lines (grid-stride over the device count)
+// float64 solve of the queued lines: one warp per line.  The warp walks the line's
+// entries in chunks of 32 (lane l gathers entry e0 + l: its factor row and value into
+// shared memory), and each lane accumulates its share of the Gram lower triangle and
+// right-hand side elements (element lane + 32 p) in float64 over the chunk; the
+// first lane then factors and solves in float64.
 template <int RP>
-__global__ void __launch_bounds__(64) k_als_retry(AlsQueue<RP> q, float lam_rel, float* __restrict__ Fout,
-                                                  int32_t* __restrict__ n_fp64) {
-    constexpr int NA = RP * (RP + 1) / 2;
-    const int n = min((int64_t)*q.count, q.cap);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        const float* gq = q.gram + (int64_t)t * AlsQueue<RP>::kVals;
-        double a[NA], b[RP];
+__global__ void __launch_bounds__(128) k_als_retry(AlsQueue<RP> q, Omega om, bool rows_side,
+                                                   const float* __restrict__ Fin, int R, float lam_rel,
+                                                   float* __restrict__ Fout, int32_t* __restrict__ n_fp64) {
+    constexpr int NA = RP * (RP + 1) / 2, NV = NA + RP, PER = (NV + 31) / 32;
+    __shared__ float xs[4][32][RP + 1];
+    __shared__ float av[4][32];
+    __shared__ double gs[4][NV];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int ei[PER], ek[PER];  // owned element: Gram (ei, ek) with ek <= ei, or b_ei (ek = -1); ei = -1 for none
 #pragma unroll
-        for (int i = 0; i < NA; ++i) a[i] = gq[i];
+    for (int p = 0; p < PER; ++p) {
+        const int e = lane + 32 * p;
+        ei[p] = -1;
+        ek[p] = -1;
+        if (e < NA) {
+            int i = 0;
+            while ((i + 1) * (i + 2) / 2 <= e) ++i;
+            ei[p] = i;
+            ek[p] = e - i * (i + 1) / 2;
+        } else if (e < NV) {
+            ei[p] = e - NA;
+        }
+    }
+    const uint16_t* sidx = rows_side ? om.sidx_r : om.sidx_c;
+    const float* sval = rows_side ? om.sval_r : om.sval_c;
+    const int n = (int)min((int64_t)*q.count, q.cap);
+    for (int t = blockIdx.x * 4 + w; t < n; t += gridDim.x * 4) {
+        const int len = q.len[t], G = q.grp[t], r = q.rank[t];
+        const int64_t slot = q.slot[t];
+        const float* src = Fin + q.src[t];
+        double acc[PER];
 #pragma unroll
-        for (int i = 0; i < RP; ++i) b[i] = gq[NA + i];
-        const int r = q.rank[t];
-        chol_solve<RP, double>(a, b, r, lam_rel, false);
-        float* d = Fout + q.dst[t];
+        for (int p = 0; p < PER; ++p) acc[p] = 0.0;
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            if (e < len) {
+                const int u = e % G, kk = e / G;
+                const int64_t pos = slot + 4 * u + 128 * (kk >> 2) + (kk & 3);
+                const int j = sidx[pos];
+                av[w][lane] = sval[pos];
 #pragma unroll
-        for (int i = 0; i < RP; ++i)
-            if (i < r) d[i] = (float)b[i];
-        atomicAdd(n_fp64, 1);
+                for (int c = 0; c < RP; ++c) xs[w][lane][c] = c < r ? src[(int64_t)j * R + c] : 0.f;
+            }
+            __syncwarp();
+            const int ne = min(32, len - e0);
+            for (int k2 = 0; k2 < ne; ++k2) {
+#pragma unroll
+                for (int p = 0; p < PER; ++p) {
+                    if (ei[p] >= 0) {
+                        const double xi = (double)xs[w][k2][ei[p]];
+                        const double xk = ek[p] >= 0 ? (double)xs[w][k2][ek[p]] : (double)av[w][k2];
+                        acc[p] = fma(xi, xk, acc[p]);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int p = 0; p < PER; ++p)
+            if (lane + 32 * p < NV) gs[w][lane + 32 * p] = acc[p];
+        __syncwarp();
+        if (lane == 0) {
+            double a[NA], b[RP];
+            for (int i = 0; i < NA; ++i) a[i] = gs[w][i];
+            for (int i = 0; i < RP; ++i) b[i] = gs[w][NA + i];
+            chol_solve<RP, double>(a, b, r, lam_rel, false);
+            float* d = Fout + q.dst[t];
+            for (int i = 0; i < RP; ++i)
+                if (i < r) d[i] = (float)b[i];
+            atomicAdd(n_fp64, 1);
+        }
+        __syncwarp();
     }
 }
 
@@ -1242,16 +1297,18 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const int stage_rows = (int)std::min<int64_t>((110 * 1024) / row_bytes, std::max<int64_t>(mr, C));
     const size_t dyn = (size_t)stage_rows * row_bytes;
     const int64_t cap = std::min<int64_t>(std::max<int64_t>(f->m, (int64_t)S * C), 1 << 18);
-    int64_t* qdst = nullptr;
-    float* qgram = nullptr;
-    int32_t* qrank = nullptr;
+    int64_t *qdst = nullptr, *qslot = nullptr, *qsrc = nullptr;
+    int32_t *qlen = nullptr, *qgrp = nullptr, *qrank = nullptr;
     if (om.sell) {
-        const int kv = RP * (RP + 1) / 2 + RP;
-        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, (size_t)cap * (12 + (size_t)kv * 4) + 1024, &st);
+        const size_t a8 = ((size_t)cap * 8 + 255) & ~(size_t)255, a4 = ((size_t)cap * 4 + 255) & ~(size_t)255;
+        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, 3 * a8 + 3 * a4, &st);
         if (!qp) return st;
         qdst = (int64_t*)qp;
-        qrank = (int32_t*)(qp + (((size_t)cap * 8 + 255) & ~(size_t)255));
-        qgram = (float*)((char*)qrank + (((size_t)cap * 4 + 255) & ~(size_t)255));
+        qslot = (int64_t*)(qp + a8);
+        qsrc = (int64_t*)(qp + 2 * a8);
+        qlen = (int32_t*)(qp + 3 * a8);
+        qgrp = (int32_t*)(qp + 3 * a8 + a4);
+        qrank = (int32_t*)(qp + 3 * a8 + 2 * a4);
         if (RP == 8)
             LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
         else
@@ -1272,18 +1329,18 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
             float* fout = rows ? uv->U : uv->V;
             int32_t* cnt = qcount + 2 * it + side;
             if (om.sell && RP == 8) {
-                AlsQueue<8> q{cnt, qdst, qgram, cap, ctx->d_status, qrank};
+                AlsQueue<8> q{cnt, qdst, qslot, qsrc, qlen, qgrp, qrank, cap, ctx->d_status};
                 k_als_line<8><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, R, rk, rows, fin, fout, lam_rel, q,
                                                               stage_rows);
                 LT_LAUNCH_CHECK(ctx, "k_als_line");
-                k_als_retry<8><<<2 * nsm, 64, 0, ctx->stream>>>(q, lam_rel, fout, n64);
+                k_als_retry<8><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
                 LT_LAUNCH_CHECK(ctx, "k_als_retry");
             } else if (om.sell) {
-                AlsQueue<16> q{cnt, qdst, qgram, cap, ctx->d_status, qrank};
+                AlsQueue<16> q{cnt, qdst, qslot, qsrc, qlen, qgrp, qrank, cap, ctx->d_status};
                 k_als_line<16><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, R, rk, rows, fin, fout, lam_rel, q,
                                                                stage_rows);
                 LT_LAUNCH_CHECK(ctx, "k_als_line");
-                k_als_retry<16><<<2 * nsm, 64, 0, ctx->stream>>>(q, lam_rel, fout, n64);
+                k_als_retry<16><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
                 LT_LAUNCH_CHECK(ctx, "k_als_retry");
             }
             if (om.csr) {
@@ -1293,6 +1350,18 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
             }
         }
     }
+    return LT_OK;
+}
+
+extern "C" lt_status lt_complete_fp64_lines(lt_ctx* ctx, int64_t* count_host) {
+    if (!ctx || !count_host) return lt_fail(ctx, LT_EINVAL, "lt_complete_fp64_lines: bad arguments");
+    *count_host = 0;
+    if (!ctx->scr[SCR_ALS]) return LT_OK;  // no lt_complete ran on this context yet
+    cudaSetDevice(ctx->device);
+    int32_t v = 0;  // word 0 of the ALS scratch: the float64 count of the last lt_complete
+    LT_CUDA(ctx, cudaMemcpyAsync(&v, ctx->scr[SCR_ALS], sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *count_host = v;
     return LT_OK;
 }
 

@@ -466,6 +466,33 @@ extern "C" lt_status lt_build_tree(lt_ctx* ctx, const float* vpls, int64_t n, lt
 }
 
 // ------------------------------------------------------------------ global cut
+namespace {
+// est[nr] and err[C] of the cut (device arrays); the refinement's per-round errors.
+lt_status cut_errors(lt_ctx* ctx, const lt_tree* tree, const float* pts, int64_t m, const float* vpls,
+                     const int32_t* rows, int64_t nr, const int32_t* cut, int C, float d_min, float* est, float* err) {
+    const int blocks = std::max(1, 8 * ctx->num_sms);
+    k_cut_estimate<<<blocks, 256, 0, ctx->stream>>>((const float4*)pts, m, (const float4*)vpls, tree->n, *tree, rows,
+                                                   nr, cut, C, d_min * d_min, est);
+    LT_LAUNCH_CHECK(ctx, "k_cut_estimate");
+    k_cut_error<<<blocks, 256, 0, ctx->stream>>>((const float4*)pts, m, *tree, rows, nr, cut, C, est, d_min * d_min,
+                                                err);
+    LT_LAUNCH_CHECK(ctx, "k_cut_error");
+    return LT_OK;
+}
+}  // namespace
+
+extern "C" lt_status lt_cut_errors(lt_ctx* ctx, const lt_tree* tree, const float* pts, int64_t m, const float* vpls,
+                                   const int32_t* rows, int64_t nr, const int32_t* cut, int32_t C, float d_min,
+                                   float* err) {
+    if (!ctx || !tree_ok(tree) || !pts || !vpls || !rows || nr < 1 || m < 1 || !cut || C < 1 || !err)
+        return lt_fail(ctx, LT_EINVAL, "lt_cut_errors: bad arguments");
+    cudaSetDevice(ctx->device);
+    lt_status st;
+    float* est = (float*)lt_scratch(ctx, SCR_CUT, (size_t)nr * 4 + 256, &st);
+    if (!est) return st;
+    return cut_errors(ctx, tree, pts, m, vpls, rows, nr, cut, C, d_min, est, err);
+}
+
 extern "C" lt_status lt_build_global_cut(lt_ctx* ctx, const lt_tree* tree, const float* pts, int64_t m,
                                          const float* vpls, const int32_t* rows, int64_t nr, float eps,
                                          int32_t max_cut, float growth, float d_min, int32_t* cut,
@@ -486,16 +513,11 @@ extern "C" lt_status lt_build_global_cut(lt_ctx* ctx, const lt_tree* tree, const
     float* err = (float*)(p + ((nr * 4 + 255) & ~255LL));
     std::vector<int32_t> cur = {0};
     std::vector<float> herr;
-    const int blocks = std::max(1, 8 * ctx->num_sms);
     for (int round = 0; round < 4096; ++round) {
         const int C = (int)cur.size();
         LT_CUDA(ctx, cudaMemcpyAsync(cut, cur.data(), C * 4, cudaMemcpyHostToDevice, ctx->stream));
-        k_cut_estimate<<<blocks, 256, 0, ctx->stream>>>((const float4*)pts, m, (const float4*)vpls, n, *tree, rows,
-                                                       nr, cut, C, d_min * d_min, est);
-        LT_LAUNCH_CHECK(ctx, "k_cut_estimate");
-        k_cut_error<<<blocks, 256, 0, ctx->stream>>>((const float4*)pts, m, *tree, rows, nr, cut, C, est,
-                                                    d_min * d_min, err);
-        LT_LAUNCH_CHECK(ctx, "k_cut_error");
+        st = cut_errors(ctx, tree, pts, m, vpls, rows, nr, cut, C, d_min, est, err);
+        if (st != LT_OK) return st;
         herr.resize(C);
         LT_CUDA(ctx, cudaMemcpyAsync(herr.data(), err, C * 4, cudaMemcpyDeviceToHost, ctx->stream));
         LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));

@@ -92,6 +92,8 @@ _SIGS = {
     "lt_build_tree": (_i32, [_p, _p, _i64, ctypes.POINTER(lt_tree)]),
     "lt_build_global_cut": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i64, _p, _p, _i64, _f32, _i32, _f32, _f32,
                                    _p, ctypes.POINTER(_i32)]),
+    "lt_cut_errors": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i64, _p, _p, _i64, _p, _i32, _f32, _p]),
+    "lt_complete_fp64_lines": (_i32, [_p, ctypes.POINTER(_i64)]),
     "lt_cut_forest": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i32, _p, _p, _i32, _p, ctypes.POINTER(_i32)]),
     "lt_make_slices": (_i32, [_p, _p, _i64, _i32, _i32, _f32, _p, _p]),
     "lt_permute_points": (_i32, [_p, _p, _i64, _p, _p]),
@@ -281,6 +283,14 @@ def lt_build_global_cut(ctx: Context, tree: Tree, pts, vpls, rows, eps, max_cut,
         ctx.h, ctypes.byref(s), _ptr(pts), pts.shape[1], _ptr(vpls), _ptr(rows), rows.shape[0], eps, max_cut,
         growth, d_min, _ptr(cut), ctypes.byref(size)))
     return cut[:size.value].clone()
+
+
+def lt_cut_errors(ctx: Context, tree: Tree, pts, vpls, rows, cut, d_min=0.01) -> torch.Tensor:
+    err = torch.empty(cut.shape[0], dtype=torch.float32, device=cut.device)
+    ctx._check("lt_cut_errors", ctx.lib.lt_cut_errors(ctx.h, ctypes.byref(tree.struct()), _ptr(pts), pts.shape[1],
+                                                      _ptr(vpls), _ptr(rows), rows.shape[0], _ptr(cut),
+                                                      cut.shape[0], d_min, _ptr(err)))
+    return err
 
 
 def lt_cut_forest(ctx: Context, tree: Tree, cut: torch.Tensor, max_levels: int = 256):
@@ -479,6 +489,12 @@ def lt_eval_stats(ctx: Context, frame: Frame, smp: Samples, d_min) -> dict:
 def lt_complete(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, lam_rel, seed):
     ctx._check("lt_complete", ctx.lib.lt_complete(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
                                                   iters, lam_rel, seed, ctypes.byref(uv.struct())))
+
+
+def lt_complete_fp64_lines(ctx: Context) -> int:
+    n = _i64(0)
+    ctx._check("lt_complete_fp64_lines", ctx.lib.lt_complete_fp64_lines(ctx.h, ctypes.byref(n)))
+    return int(n.value)
 
 
 def lt_complete_adm(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, alpha_rel, gamma, seed):

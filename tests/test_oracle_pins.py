@@ -403,6 +403,24 @@ def test_als_fully_observed_reaches_truncated_svd():
     assert abs(err - best) / best < 1e-6
 
 
+@pytest.mark.parametrize("n_s,R,cols,want", [
+    # values worked out by hand from r_s = min(R, max(8, 8 * ceil(n' / cols)))
+    (0, 32, 512, 8), (1, 32, 512, 8), (511, 32, 512, 8), (512, 32, 512, 8), (513, 32, 512, 16),
+    (1024, 32, 512, 16), (1025, 32, 512, 24), (1536, 32, 512, 24), (1537, 32, 512, 32),
+    (2049, 32, 512, 32), (4 * 512 + 1, 32, 512, 32), (100000, 32, 512, 32),
+    (513, 16, 512, 16), (2000, 16, 512, 16), (1, 8, 512, 8), (5000, 8, 512, 8),
+    (100, 32, 100, 8), (101, 32, 100, 16), (301, 32, 100, 32)])
+def test_slice_rank_rule(n_s, R, cols, want):
+    """The per-slice rank rule (configuration 3: rank 8-32 chosen per slice) against
+    hand-computed values at and one past every multiple of the column quantum."""
+    assert pipeline.slice_rank({"rank": R, "rank_cols": cols}, n_s) == want
+
+
+def test_slice_rank_fixed_without_columns():
+    assert pipeline.slice_rank({"rank": 16, "rank_cols": 0}, 5000) == 16
+    assert pipeline.slice_rank({"rank": 24}, 3) == 24
+
+
 # --------------------------------------------------------------------------- render
 def test_render_factorised_sum_equals_explicit_sum():
     rng = np.random.default_rng(6)
