@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames-only", type=int, default=0,
+                    help="for profilers: set up, render this many plain frames and one graph replay, print no line")
     return ap.parse_args()
 
 
@@ -456,6 +458,14 @@ def run_ours(args):
     for i in range(args.warmup):
         frame(i)
     lt.lt_sync(ctx)
+    if args.frames_only:
+        for i in range(args.frames_only):
+            frame(100 + i)
+        g_only = lt.lt_frame_graph_capture(ctx, R.frame, lt.params(cfg), R.smp, R.uv, R.row_perm, R.img)
+        lt.lt_frame_graph_launch(g_only, seed0 + 200)
+        lt.lt_sync(ctx)
+        torch.cuda.synchronize()
+        return
     # the batched form: the whole frame as one CUDA graph, pass 2 from the learned
     # proposal (or from g when no trained network is shipped)
     prm_g = lt.params(cfg)
