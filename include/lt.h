@@ -125,6 +125,11 @@ int64_t lt_launch_count(const lt_ctx* ctx);
 /* Device address and size of scratch slot `slot` of the context (debugging aid:
  * the layout of a slot is internal and may change). */
 lt_status lt_debug_scratch(lt_ctx* ctx, int32_t slot, void** ptr, int64_t* bytes);
+/* Cap the device scratch the context may hold: a call whose scratch would grow the
+ * context's total beyond `bytes` fails with LT_ENOMEM before allocating (what the
+ * context already holds stays valid).  0 removes the cap.  For hosts that give the
+ * library a fixed device-memory budget, and for tests of the out-of-memory path. */
+lt_status lt_set_scratch_limit(lt_ctx* ctx, int64_t bytes);
 
 /* Occluders for the shadow rays (Sec. 6 casts rays against the scene; here a
  * uniform grid over the boxes, res^3 cells, res 0 = automatic).  The grid is built
@@ -241,11 +246,14 @@ lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min, lt_sample
  * stall the device mid-frame.  Arguments, results and errors are those of
  * lt_eval_entries; the per-slice prefix it needs lives in a fixed device array of
  * the library (32 KB on every GPU that loads the library, held until exit), so
- * at most 4096 slices are accepted (LT_EINVAL beyond that).  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make it
- * before any stream capture.  All calls share the array and it keeps the last
- * call's contents: calls whose work overlaps on the GPU (other streams or
- * contexts) race on it and must be serialised by the caller. */
+ * at most 4096 slices are accepted (LT_EINVAL beyond that).  Each call looks up
+ * that array's device address (cudaGetSymbolAddress, which allocates nothing), so
+ * the library keeps working after a device reset; during a stream capture the
+ * lookup is not made and the address of the device's last call is used, so make
+ * one call on the device before capturing (a first call inside a capture returns
+ * LT_EINVAL).  All calls share the array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other streams or contexts) race on it and
+ * must be serialised by the caller. */
 lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, float d_min, lt_samples* smp);
 /* Instrumentation (no counterpart in the paper): re-runs the evaluation of the same
  * entries without storing values and returns in stats_host[4] the entries, the shadow

@@ -54,6 +54,16 @@ void* lt_scratch(lt_ctx* ctx, int slot, size_t bytes, lt_status* st) {
         ctx->scr_size[slot] = 0;
     }
     size_t want = bytes + bytes / 4;
+    if (ctx->scratch_limit > 0) {  // a caller's device-memory budget for this context
+        size_t held = 0;
+        for (int k = 0; k < SCR_NSLOTS; ++k) held += ctx->scr_size[k];
+        if ((int64_t)(held + bytes) > ctx->scratch_limit) {
+            *st = lt_fail(ctx, LT_ENOMEM, "scratch limit of " + std::to_string(ctx->scratch_limit) +
+                                              " bytes reached (" + std::to_string(held + bytes) + " needed)");
+            return nullptr;
+        }
+        if ((int64_t)(held + want) > ctx->scratch_limit) want = bytes;
+    }
     cudaError_t e = cudaMalloc(&ctx->scr[slot], want);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -125,6 +135,12 @@ extern "C" lt_status lt_set_tuning(lt_ctx* ctx, const lt_tuning* t) {
 }
 
 extern "C" int64_t lt_launch_count(const lt_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" lt_status lt_set_scratch_limit(lt_ctx* ctx, int64_t bytes) {
+    if (!ctx || bytes < 0) return lt_fail(ctx, LT_EINVAL, "lt_set_scratch_limit: bad arguments");
+    ctx->scratch_limit = bytes;
+    return LT_OK;
+}
 
 extern "C" lt_status lt_debug_scratch(lt_ctx* ctx, int32_t slot, void** ptr, int64_t* bytes) {
     if (!ctx || slot < 0 || slot >= SCR_NSLOTS || !ptr || !bytes) return LT_EINVAL;

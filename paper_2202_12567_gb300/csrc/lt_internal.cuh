@@ -467,6 +467,7 @@ struct lt_ctx {
     std::vector<void*> retired;            // scratch that live graphs may still reference
     int graphs = 0;                        // graphs alive on this context
     lt_tuning tune{16, 16, 96};            // launch tuning (lt_set_tuning)
+    int64_t scratch_limit = 0;             // bytes of scratch the context may hold (0: no limit)
 };
 
 inline ltk::SeedRef seed_ref(const lt_ctx* ctx, uint64_t seed) { return ltk::SeedRef{seed, ctx->seed_dev}; }

@@ -206,7 +206,7 @@ __global__ void k_p1_kpfx(lt_frame F, P1Plan pl, int64_t* kpfx) {
 
 // -- initial entries of every cut node of every slice (one shadow ray per thread)
 __global__ void __launch_bounds__(128) k_p1_initial(lt_frame F, Grid g, float dmin2, P1Plan pl, P1Store st,
-                                                    const int64_t* __restrict__ kpfx) {
+                                                    const int64_t* __restrict__ kpfx, int32_t* status) {
     const float4* pts = reinterpret_cast<const float4*>(F.pts);
     const float4* vpls = reinterpret_cast<const float4*>(F.vpls);
     const int C = F.C, NF = 2 * C - 1;
@@ -233,7 +233,9 @@ __global__ void __launch_bounds__(128) k_p1_initial(lt_frame F, Grid g, float dm
         const int node = F.forest[8 * c];
         const PointRec P = load_rec(pts, F.m, F.slice_off[s] + st.rows[slot]);
         const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
-        st.v0[slot] = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
+        const float v = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
+        if (!isfinite(v)) latch(status, LT_ENUMERIC);  // a non-finite input (flux, albedo, position)
+        st.v0[slot] = v;
     }
 }
 
@@ -542,7 +544,8 @@ __global__ void __launch_bounds__(256) k_p1_setup_big(lt_frame F, P1Plan pl, P1S
 }
 
 // -- level h, step 2: the queued entries, one shadow ray per thread
-__global__ void __launch_bounds__(128) k_p1_rays(lt_frame F, Grid g, float dmin2, P1Store st, P1Work w, int h) {
+__global__ void __launch_bounds__(128) k_p1_rays(lt_frame F, Grid g, float dmin2, P1Store st, P1Work w, int h,
+                                                 int32_t* status) {
     const float4* pts = reinterpret_cast<const float4*>(F.pts);
     const float4* vpls = reinterpret_cast<const float4*>(F.vpls);
     const int64_t n = min(w.mcount[h], w.mcap);
@@ -550,7 +553,9 @@ __global__ void __launch_bounds__(128) k_p1_rays(lt_frame F, Grid g, float dmin2
         const int node = w.mnode[q];
         const PointRec P = load_rec(pts, F.m, w.mpt[q]);
         const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
-        st.v0[w.mdst[q]] = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
+        const float v = entry_value(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g);
+        if (!isfinite(v)) latch(status, LT_ENUMERIC);
+        st.v0[w.mdst[q]] = v;
     }
 }
 
@@ -1012,7 +1017,7 @@ __global__ void k_count_prefix(const lt_samples smp, int S, int64_t* pfx) {
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_eval_entries(lt_frame F, Grid g, float dmin2, lt_samples smp,
                                                       const int64_t* __restrict__ pfx,
-                                                      unsigned long long* __restrict__ stats) {
+                                                      unsigned long long* __restrict__ stats, int32_t* status) {
     extern __shared__ int64_t spfx[];
     const int S = F.S;
     for (int i = threadIdx.x; i <= S; i += blockDim.x) spfx[i] = pfx[i];
@@ -1038,8 +1043,12 @@ __global__ void __launch_bounds__(128) k_eval_entries(lt_frame F, Grid g, float 
         const PointRec P = load_rec(pts, F.m, F.slice_off[s] + r);
         const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
         const float v = entry_value<COUNT>(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g, &wc, &rays);
-        if (COUNT) ++entries;
-        else smp.val[e] = v;
+        if (COUNT) {
+            ++entries;
+        } else {
+            if (!isfinite(v)) latch(status, LT_ENUMERIC);
+            smp.val[e] = v;
+        }
     }
     if (COUNT) {
         atomicAdd(stats + 0, (unsigned long long)entries);
@@ -1159,7 +1168,7 @@ lt_status sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, i
     k_p1_kpfx<<<1, 1024, 0, ctx->stream>>>(*f, pl, w.kpfx);
     LT_LAUNCH_CHECK(ctx, "k_p1_kpfx");
     const int ray_grid = ctx->tune.ray_ctas_per_sm * nsm;
-    k_p1_initial<<<ray_grid, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, pl, store, w.kpfx);
+    k_p1_initial<<<ray_grid, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, pl, store, w.kpfx, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_p1_initial");
     k_p1_leafmean<<<grid_for((int64_t)S * C, 256), 256, 0, ctx->stream>>>(*f, pl, store, w.leafmean);
     LT_LAUNCH_CHECK(ctx, "k_p1_leafmean");
@@ -1189,7 +1198,7 @@ lt_status sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, i
         LT_LAUNCH_CHECK(ctx, "k_p1_setup");
         k_p1_setup_big<<<4 * nsm, 256, 0, ctx->stream>>>(*f, pl, store, w, h, ctx->d_status);
         LT_LAUNCH_CHECK(ctx, "k_p1_setup_big");
-        k_p1_rays<<<ray_grid, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, store, w, h);
+        k_p1_rays<<<ray_grid, 128, 0, ctx->stream>>>(*f, ctx->grid, dmin2, store, w, h, ctx->d_status);
         LT_LAUNCH_CHECK(ctx, "k_p1_rays");
         k_p1_decide<<<grid_for(npairs, 128), 128, 0, ctx->stream>>>(*f, pl, store, w, h);
         LT_LAUNCH_CHECK(ctx, "k_p1_decide");
@@ -1265,7 +1274,7 @@ extern "C" lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
     k_eval_entries<false><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
-                                                                        nullptr);
+                                                                        nullptr, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries");
     return LT_OK;
 }
@@ -1287,19 +1296,29 @@ std::mutex g_noalloc_mu;
 int64_t* g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of g_noalloc_prefix on the context's device.  In host code the
-// symbol names a host-side stand-in, so the real address is looked up once per
-// device (with that device current) and cached.
+// symbol names a host-side stand-in, so the real address is looked up with that
+// device current.  It is looked up again on every call (cheap, and it allocates
+// nothing), so a module reloaded after a device reset is found where it now is; the
+// last address seen per device is kept only for calls made while the context's
+// stream is being captured, where the lookup is not attempted.
 lt_status noalloc_prefix(lt_ctx* ctx, int64_t** out) {
     if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
         return lt_fail(ctx, LT_EINVAL, "lt_eval_entries_noalloc: device index out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    LT_CUDA(ctx, cudaStreamIsCapturing(ctx->stream, &cap));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[ctx->device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_prefix);
-        if (e != cudaSuccess) return lt_cuda_check(ctx, e, "cudaGetSymbolAddress(g_noalloc_prefix)");
-        g_noalloc_addr[ctx->device] = (int64_t*)p;
+    if (cap != cudaStreamCaptureStatusNone) {
+        if (!g_noalloc_addr[ctx->device])
+            return lt_fail(ctx, LT_EINVAL,
+                           "lt_eval_entries_noalloc: make one call on this device before capturing a stream");
+        *out = g_noalloc_addr[ctx->device];
+        return LT_OK;
     }
-    *out = g_noalloc_addr[ctx->device];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_prefix);
+    if (e != cudaSuccess) return lt_cuda_check(ctx, e, "cudaGetSymbolAddress(g_noalloc_prefix)");
+    g_noalloc_addr[ctx->device] = (int64_t*)p;
+    *out = (int64_t*)p;
     return LT_OK;
 }
 }  // namespace
@@ -1323,7 +1342,7 @@ extern "C" lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, flo
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
     k_eval_entries<false><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
-                                                                        nullptr);
+                                                                        nullptr, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries");
     return LT_OK;
 }
@@ -1348,7 +1367,7 @@ extern "C" lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, 
                                           (int)shm));
     lt_samples copy = *smp;
     k_eval_entries<true><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, copy, pfx,
-                                                                       stats);
+                                                                       stats, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries<count>");
     unsigned long long h[4];
     LT_CUDA(ctx, cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));

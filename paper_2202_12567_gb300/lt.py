@@ -85,6 +85,7 @@ _SIGS = {
     "lt_status_word": (_p, [_p]),
     "lt_launch_count": (_i64, [_p]),
     "lt_debug_scratch": (_i32, [_p, _i32, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),
+    "lt_set_scratch_limit": (_i32, [_p, _i64]),
     "lt_scene_upload": (_i32, [_p, _p, _i64, _i32]),
     "lt_shadow_test": (_i32, [_p, _p, _p, _i64, _p]),
     "lt_eval_pairs": (_i32, [_p, _p, _i64, _p, _i64, _p, _p, _p, _i64, _f32, _p]),
@@ -209,6 +210,10 @@ def lt_debug_scratch(ctx: Context, slot: int) -> torch.Tensor:
     if not ptr.value:
         return torch.zeros(0, dtype=torch.uint8, device="cuda")
     return torch.as_tensor(_DevBuf(ptr.value, size.value), device="cuda")
+
+
+def lt_set_scratch_limit(ctx: Context, nbytes: int):
+    ctx._check("lt_set_scratch_limit", ctx.lib.lt_set_scratch_limit(ctx.h, int(nbytes)))
 
 
 def lt_sync(ctx: Context):
