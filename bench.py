@@ -15,8 +15,9 @@ against the CPU oracle).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs under torchrun: every rank renders its own frames of the same workload
-(independent problems, no collective on the data path; weak scaling).
+N > 1 runs under torchrun: one frame is split by slices over the ranks (no
+collective on the data path; the pixel blocks are gathered once for the quality
+check; strong scaling).
 --impl reference times the CPU oracle (the plain float64 restatement of the method)
 on the host cores on a bounded sample of the same frame.
 """
@@ -177,7 +178,7 @@ def run_reference(args):
               f"untimed; warm-up steps: none run (no caches or compilation on the CPU path)")
     line = dict(impl="reference", metric=METRIC, value=round(value, 1), unit="ms/frame",
                 n_gpus=args.gpus, steps=K, warmup=args.warmup, ms_per_step=round(wall * 1e3 / K, 1),
-                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                higher_is_better=False, scaling="strong", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=args.workload),
                 cpu_baseline=dict(value=round(value, 1), unit="ms/frame", cores=cores, kind="oracle",
                                   sample=sample),
@@ -395,6 +396,104 @@ def mesh_leg(args, device: int, flush) -> dict | None:
                 rays_per_pixel=round(float(R.rays()) / R.frame.m, 2))
 
 
+def run_sharded(args, world: int, rank: int, local: int):
+    """N > 1: one frame split by slices over the ranks (strong scaling).  Every rank
+    sets up the frame, renders its longest-processing-time share of the slices as a
+    captured graph (each slice with its index in the whole frame, so the pixels are
+    the whole frame's), and the frame time is the slowest rank's; the pixel blocks are
+    gathered once on rank 0 for the quality check."""
+    import torch
+    import torch.distributed as dist
+
+    from ltinputs import get_config, make_scene
+    from paper_2202_12567_gb300 import lt, shard
+    from paper_2202_12567_gb300.renderer import Renderer
+
+    # the ranks exchange only host values (frame times, the final pixel blocks): gloo
+    dist.init_process_group("gloo", init_method="env://")
+    local = local % torch.cuda.device_count()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = get_config(args.workload)
+    sc = make_scene(cfg)
+    R = Renderer(sc, cfg, device=local).setup()
+    parts = shard.lpt_partition(shard.slice_costs(R.slice_off.cpu().numpy(), C=R.frame.C), world)
+    sub = shard.shard_renderer(R, parts[rank])
+    seed0 = cfg["frame_seed"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if sub is not None:
+        sub.capture()
+        for i in range(args.warmup):
+            sub.render_graph(seed0 + 100 + i)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    launches0 = lt.lt_launch_count(R.ctx)
+    ms = []
+    for k in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if sub is not None:
+            lt.lt_frame_graph_launch(sub.graph, seed0 + 1000 + k)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    launches = lt.lt_launch_count(R.ctx) - launches0
+    med = shard.max_over_ranks(float(statistics.median(ms)))
+    total = shard.max_over_ranks(float(sum(ms)))
+    dist.barrier()
+    # end to end: this rank's points in from pinned memory, its graph, its pixels out
+    e2e = []
+    if sub is not None:
+        pts_h = sub.pts_s.cpu().pin_memory()
+        out_h = torch.empty(sub.pixels.numel(), dtype=torch.float32).pin_memory()
+    for k in range(max(3, args.steps // 2) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        if sub is not None:
+            sub.pts_s.copy_(pts_h, non_blocking=True)
+            lt.lt_frame_graph_launch(sub.graph, seed0 + 5000 + k)
+            out_h.copy_(sub.img[sub.pixels], non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e.append(a.elapsed_time(b))
+    e2e_ms = shard.max_over_ranks(float(statistics.median(e2e)))
+    h2d = int(sub.pts_s.numel() * 4) if sub is not None else 0
+    d2h = int(sub.pixels.numel() * 4) if sub is not None else 0
+    h2d = int(shard.max_over_ranks(h2d))
+    d2h = int(shard.max_over_ranks(d2h))
+    # quality of the last timed frame, gathered on rank 0
+    if sub is not None:
+        lt.lt_frame_graph_launch(sub.graph, seed0 + 1000 + args.steps - 1)
+        lt.lt_sync(R.ctx)
+        pixels, values = sub.pixels.cpu(), sub.img[sub.pixels].cpu()
+    else:
+        pixels, values = torch.zeros(0, dtype=torch.int64), torch.zeros(0)
+    img = shard.gather_image(pixels, values, sc.m)
+    if rank == 0:
+        bf = R.bruteforce().double().cpu()
+        rel = float(torch.linalg.norm(img.double() - bf) / torch.linalg.norm(bf))
+        line = dict(metric=METRIC, value=round(med, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=round(total / args.steps, 4), higher_is_better=False,
+                    scaling="strong", vs_baseline=None, dtype="f32", data="synthetic",
+                    config=dict(workload=f"{args.workload}: one frame split by slices over {world} GPUs "
+                                         f"(longest-processing-time on m' n'; slices per rank "
+                                         f"{[len(p) for p in parts]}), each rank's share as one captured graph",
+                                l2="flushed (256 MB write) between timed frames",
+                                rel_rmse_vs_bruteforce=round(rel, 5)),
+                    e2e=dict(value=round(e2e_ms, 4), unit="ms/frame", h2d_bytes_per_step=h2d,
+                             d2h_bytes_per_step=d2h),
+                    gpu_launches=int(launches), clocks=clk)
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -408,7 +507,7 @@ def run_ours(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
+        return run_sharded(args, world, rank, local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     peaks = {}
@@ -493,8 +592,6 @@ def run_ours(args):
             ms.append(a.elapsed_time(b))
         return ms
 
-    if world > 1:
-        dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     launches0 = lt.lt_launch_count(ctx)
@@ -503,13 +600,7 @@ def run_ours(args):
     launches = lt.lt_launch_count(ctx) - launches0
     lt.lt_sync(ctx)
     total_ms = float(sum(per))
-    med_ms = float(statistics.median(per))
-    if world > 1:
-        from paper_2202_12567_gb300 import shard
-        total_ms = shard.max_over_ranks(total_ms, device=dev)
-        med_ms = shard.max_over_ranks(med_ms, device=dev)
-        dist.barrier()
-    ms_frame = med_ms / world  # median replay, max over ranks; every rank renders its own frames
+    ms_frame = float(statistics.median(per))  # median replay
     img = R.img.clone()
     # the same graph with the paper's pdf g (seeds as above: the same pass-1 draws)
     per_g = replay(graph_g, 1000)
@@ -630,7 +721,7 @@ def run_ours(args):
 
     line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
-                scaling="weak", vs_baseline=None, dtype="f32", data="synthetic",
+                scaling="strong", vs_baseline=None, dtype="f32", data="synthetic",
                 config=dict(workload=f"{args.workload}: {sc.width}x{sc.height} points, {sc.n} VPLs, {sc.nb} boxes, "
                                      f"{cfg['n_slices']} slices, {100 * cfg['rate']:g}% sampling, rank {cfg['rank']}, "
                                      f"{cfg['als_iters']} ALS sweeps, cut <= {cfg['max_cut']}, tau {cfg['tau']}",
@@ -665,10 +756,7 @@ def run_ours(args):
         except Exception as e:  # report, do not hide
             line["cpu_baseline"] = dict(value=None, unit="ms/frame", cores=host_cores(), kind="oracle",
                                         sample=f"failed: {e}")
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    print(json.dumps(line), flush=True)
 
 
 def main():

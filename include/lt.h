@@ -84,6 +84,11 @@ typedef struct {
     const int32_t* level_off;  /* [H+2] internal forest nodes of height h: level_nodes[level_off[h]..] */
     const int32_t* level_nodes;/* [C-1] */
     int32_t H;                 /* forest height (host value) */
+    const int32_t* slice_id;   /* [S] the index each slice has in the whole frame, used in every random
+                                  counter that names a slice (pass-1 rows, pass-2 draws, completion
+                                  starts), or NULL for s.  A process that renders a subset of a frame's
+                                  slices (the frame split over GPUs by slices) passes their indices
+                                  in the whole frame and draws exactly what the whole frame draws. */
 } lt_frame;
 
 /* Per-slice sampled entries Omega_s (Sec. 4-5).  Entry keys pack (row << 16) | col

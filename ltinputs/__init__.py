@@ -8,6 +8,6 @@ that both the CPU oracle and the CUDA path can consume the same arrays without
 sharing any of the code under test.
 """
 from .configs import CONFIGS, get_config
-from .scenes import make_scene, Scene
+from .scenes import load_or_make_scene, make_scene, Scene
 
-__all__ = ["CONFIGS", "get_config", "make_scene", "Scene"]
+__all__ = ["CONFIGS", "get_config", "load_or_make_scene", "make_scene", "Scene"]

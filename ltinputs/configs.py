@@ -98,3 +98,12 @@ CONFIGS["room64_vpl1k_mesh"] = dict(
 CONFIGS["room256_vpl16k_mesh"] = dict(
     CONFIGS["room256_vpl16k_2box"], n_meshes=6, mesh_subdiv=3, scene_seed=5001,
 )
+
+# 1024x1024 points, 262144 VPLs, 2000 boxes with a Phong lobe on 30% of faces,
+# 256 k-means slices, rank up to 32 chosen per slice (the large combined workload,
+# sized like the paper's Tearoom: 786K pixels, 231K VPLs).
+CONFIGS["room1024_vpl256k_2000box_glossy"] = dict(
+    _BASE, width=1024, height=1024, n_vpl=262144, n_big_boxes=0, n_small_boxes=2000,
+    glossy_frac=0.3, n_slices=256, rate=0.05, rate1=0.002, rank=32, rank_cols=512, als_iters=10,
+    max_cut=16384, tau=0.0005, scene_seed=1005,
+)

@@ -417,3 +417,29 @@ def single_quad_scene(vpl_pos, vpl_nrm, vpl_flux, vpl_albedo, quad_y: float, res
     vpls[2, 0, :3] = vpl_nrm
     vpls[2, 0, 3] = vpl_flux
     return points, vpls
+
+
+_CACHE_FIELDS = ("boxes", "points", "vpls")
+
+
+def load_or_make_scene(cfg: dict, cache_dir: str | None = None) -> Scene:
+    """make_scene(cfg), stored in and reloaded from ``cache_dir`` (an .npz per scene
+    recipe) so that large scenes are generated once; None: no cache."""
+    if cache_dir is None or cfg.get("rgb") or int(cfg.get("n_meshes", 0)):
+        return make_scene(cfg)
+    import hashlib
+    import json
+    import os
+    keys = ("width", "height", "n_vpl", "n_big_boxes", "n_small_boxes", "glossy_frac", "scene_seed",
+            "light_power", "light_size")
+    tag = hashlib.sha1(json.dumps({k: cfg.get(k) for k in keys}, sort_keys=True).encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir, f"scene_{tag}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        return Scene(cfg=cfg, boxes=z["boxes"], points=z["points"], vpls=z["vpls"], width=int(cfg["width"]),
+                     height=int(cfg["height"]), n_emitted=int(z["n_emitted"]))
+    sc = make_scene(cfg)
+    os.makedirs(cache_dir, exist_ok=True)
+    np.savez(path + ".tmp.npz", boxes=sc.boxes, points=sc.points, vpls=sc.vpls, n_emitted=sc.n_emitted)
+    os.replace(path + ".tmp.npz", path)
+    return sc

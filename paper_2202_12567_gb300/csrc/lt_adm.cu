@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
         const int j = clo + (int)(e / R), c = (int)(e % R);
         float v = 0.f;
         if (c < r) {
-            const uint32_t w = philox((uint32_t)c, (uint32_t)j, (uint32_t)s, kTagAlsInit, seed).x;
+            const uint32_t w = philox((uint32_t)c, (uint32_t)j, slice_key(F.slice_id, s), kTagAlsInit, seed).x;
             v = amp * (0.5f + (float)w * 2.3283064365386963e-10f);
         }
         const int64_t at = (int64_t)j * R + c;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(kAdmThreads, 2) k_adm(lt_frame F, lt_samples s
         const int i = rlo + (int)(e / R), c = (int)(e % R);
         float v = 0.f;
         if (c < r) {
-            const uint32_t w = philox((uint32_t)c, (uint32_t)i, (uint32_t)s, kTagAdmInit, seed).x;
+            const uint32_t w = philox((uint32_t)c, (uint32_t)i, slice_key(F.slice_id, s), kTagAdmInit, seed).x;
             v = amp * (0.5f + (float)w * 2.3283064365386963e-10f);
         }
         const int64_t at = (int64_t)(row0 + i) * R + c;

@@ -381,7 +381,7 @@ __global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int R, const in
             V[((int64_t)s * F.C + j) * R + k] = 0.f;
             continue;
         }
-        const uint32_t w = philox((uint32_t)k, (uint32_t)j, (uint32_t)s, kTagAlsInit, seed).x;
+        const uint32_t w = philox((uint32_t)k, (uint32_t)j, slice_key(F.slice_id, s), kTagAlsInit, seed).x;
         V[((int64_t)s * F.C + j) * R + k] = amp * (0.5f + (float)w * 2.3283064365386963e-10f);
     }
 }

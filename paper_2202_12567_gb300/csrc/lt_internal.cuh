@@ -59,6 +59,11 @@ __host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
     return {c0, c1, c2, c3};
 }
 
+// The slice index a random counter uses: the slice's index in the whole frame.
+__device__ __forceinline__ uint32_t slice_key(const int32_t* slice_id, int s) {
+    return slice_id ? (uint32_t)slice_id[s] : (uint32_t)s;
+}
+
 // floor(w * size / 2^32)
 __host__ __device__ inline uint32_t uniform_index(uint32_t w, uint32_t size) {
     return (uint32_t)(((uint64_t)w * (uint64_t)size) >> 32);

@@ -154,7 +154,7 @@ __global__ void k_p1_draws(lt_frame F, SeedRef sr, P1Plan pl, P1Store st, int32_
             got = ms;
         } else {
             for (int t = 0; got < k && t < kMaxDraws; ++t) {
-                const int v = (int)uniform_index(philox((uint32_t)t, (uint32_t)x, (uint32_t)s, kTagPass1, seed).x,
+                const int v = (int)uniform_index(philox((uint32_t)t, (uint32_t)x, slice_key(F.slice_id, s), kTagPass1, seed).x,
                                                  (uint32_t)ms);
                 bool dup = false;
                 for (int q = 0; q < got; ++q) dup |= (r[q] == v);
@@ -910,7 +910,7 @@ __global__ void __cluster_dims__(kP2Cluster, 1, 1) __launch_bounds__(kP2Block, 2
 #pragma unroll
         for (int d = 0; d < kP2Draws; ++d) {  // draw and column search, all draws at once
             tt[d] = t0 + rank * per_cta + (int64_t)threadIdx.x * kP2Draws + d;
-            const U4 x = philox((uint32_t)tt[d], 0u, (uint32_t)s, kTagPass2, seed);
+            const U4 x = philox((uint32_t)tt[d], 0u, slice_key(F.slice_id, s), kTagPass2, seed);
             u[d] = (unsigned long long)x.x * th + (((unsigned long long)x.x * tl) >> 32);
             wrow[d] = x.y;
             home[d] = -1;

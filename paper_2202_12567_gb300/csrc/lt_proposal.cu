@@ -659,7 +659,8 @@ __device__ void mgs_cols(float* Q, int n, int r, float* red) {
     }
 }
 
-__global__ void __launch_bounds__(512) k_leverage(lt_samples smp, int S, int C, const float* __restrict__ G,
+__global__ void __launch_bounds__(512) k_leverage(lt_samples smp, const int32_t* __restrict__ slice_id, int S, int C,
+                                                  const float* __restrict__ G,
                                                   const int64_t* __restrict__ goff2, int64_t gcap, int r, int iters,
                                                   uint64_t seed, float* __restrict__ Qall, float* __restrict__ Yall,
                                                   const int32_t* __restrict__ goff, float* __restrict__ target) {
@@ -674,7 +675,7 @@ __global__ void __launch_bounds__(512) k_leverage(lt_samples smp, int S, int C, 
     const float* Gs = G + goff2[s];
     for (int e = threadIdx.x; e < ns * rr; e += blockDim.x) {
         const int c = e / rr, k = e % rr;
-        Q[e] = (float)((double)philox((uint32_t)k, (uint32_t)c, (uint32_t)s, kTagLeverage, seed).x *
+        Q[e] = (float)((double)philox((uint32_t)k, (uint32_t)c, slice_key(slice_id, s), kTagLeverage, seed).x *
                            2.3283064365386963e-10 - 0.5);
     }
     __syncthreads();
@@ -790,7 +791,8 @@ extern "C" lt_status lt_leverage_targets(lt_ctx* ctx, const lt_frame* f, const l
     const unsigned tiles = (unsigned)((nmax + 31) / 32);
     k_gram<<<dim3(tiles, tiles, S), 256, 0, ctx->stream>>>(*f, *smp, M, moff, goff2, gcap, G);
     LT_LAUNCH_CHECK(ctx, "k_gram");
-    k_leverage<<<S, 512, 0, ctx->stream>>>(*smp, S, C, G, goff2, gcap, r, iters, seed, Q, Y, group_off, target);
+    k_leverage<<<S, 512, 0, ctx->stream>>>(*smp, f->slice_id, S, C, G, goff2, gcap, r, iters, seed, Q, Y, group_off,
+                                           target);
     LT_LAUNCH_CHECK(ctx, "k_leverage");
     return LT_OK;
 }

@@ -43,7 +43,7 @@ class lt_tree(ctypes.Structure):
 class lt_frame(ctypes.Structure):
     _fields_ = [("pts", _p), ("m", _i64), ("vpls", _p), ("n", _i64), ("slice_off", _p), ("S", _i32),
                 ("max_rows", _i32), ("tree", lt_tree), ("C", _i32), ("forest", _p), ("level_off", _p),
-                ("level_nodes", _p), ("H", _i32)]
+                ("level_nodes", _p), ("H", _i32), ("slice_id", _p)]
 
 
 class lt_samples(ctypes.Structure):
@@ -331,17 +331,18 @@ def lt_permute_points(ctx: Context, pts, row_perm):
 class Frame:
     """The fixed inputs of a frame (lt_frame) and the tensors behind its pointers."""
 
-    def __init__(self, pts_s, vpls, slice_off, tree: Tree, cut, forest, level_off, level_nodes, H):
+    def __init__(self, pts_s, vpls, slice_off, tree: Tree, cut, forest, level_off, level_nodes, H, slice_id=None):
         self.pts_s, self.vpls, self.slice_off, self.tree, self.cut = pts_s, vpls, slice_off, tree, cut
         self.forest, self.level_off, self.level_nodes, self.H = forest, level_off, level_nodes, H
+        self.slice_id = slice_id  # [S] int32 device tensor: each slice's index in the whole frame, or None
         self.slice_off_host = slice_off.cpu().numpy().astype(np.int64)
         self.sizes = np.diff(self.slice_off_host)
         self.S = len(self.sizes)
         self.C = int(cut.shape[0])
         self.m = pts_s.shape[1]
         self._s = lt_frame(_ptr(pts_s), self.m, _ptr(vpls), vpls.shape[1], _ptr(slice_off), self.S,
-                           int(self.sizes.max()), tree.struct(), self.C, _ptr(forest), _ptr(level_off),
-                           _ptr(level_nodes), H)
+                           int(self.sizes.max()) if self.S else 0, tree.struct(), self.C, _ptr(forest),
+                           _ptr(level_off), _ptr(level_nodes), H, _ptr(slice_id))
 
     def struct(self) -> lt_frame:
         return self._s
@@ -401,7 +402,7 @@ class RGB:
         self._s = lt_rgb(_ptr(self.pt_ratio), _ptr(self.node_ratio), _ptr(self.slice_off3), _ptr(self.row_perm3))
         f = frame.struct()
         self._f3 = lt_frame(f.pts, 3 * frame.m, f.vpls, f.n, _ptr(self.slice_off3), f.S, 3 * f.max_rows, f.tree,
-                            f.C, f.forest, f.level_off, f.level_nodes, f.H)
+                            f.C, f.forest, f.level_off, f.level_nodes, f.H, f.slice_id)
         # stacked samples: three times the capacity of every slice
         i32 = dict(dtype=torch.int32, device=dev)
         self.off_host = 3 * smp.off_host

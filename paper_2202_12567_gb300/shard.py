@@ -9,6 +9,7 @@ NCCL between GPUs).
 """
 from __future__ import annotations
 
+import copy
 import heapq
 
 import numpy as np
@@ -84,3 +85,33 @@ def max_over_ranks(x: float, group=None, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     return float(t.item())
+
+
+def shard_renderer(R, slices):
+    """A renderer for the given slices of the frame that the set-up renderer R holds:
+    their points (slice order kept), the same VPLs, tree, cut and forest, and each
+    slice's index in the whole frame (lt_frame.slice_id), so every random draw is the
+    one the whole frame makes and the shard's pixels equal the whole frame's.  Its
+    image is full-size; only the shard's pixels (`pixels`) are written.  None when
+    `slices` is empty."""
+    from . import lt
+    if len(slices) == 0:
+        return None
+    slices = [int(s) for s in slices]
+    off = R.slice_off.cpu().numpy().astype(np.int64)
+    rows = torch.from_numpy(rows_of(off, slices)).to(R.dev)
+    sizes = [int(off[s + 1] - off[s]) for s in slices]
+    sub = copy.copy(R)
+    sub.pts_s = R.pts_s[:, rows].contiguous()
+    sub.row_perm = R.row_perm[rows].contiguous()
+    sub.slice_off = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int32, device=R.dev)
+    sub.slice_id = torch.tensor(slices, dtype=torch.int32, device=R.dev)
+    f = R.frame
+    sub.frame = lt.Frame(sub.pts_s, R.vpls, sub.slice_off, R.tree, f.cut, f.forest, f.level_off, f.level_nodes, f.H,
+                         slice_id=sub.slice_id)
+    sub.smp = lt.Samples(sub.frame, R.cfg["rate"], R.cfg["rate1"])
+    sub.uv = lt.Factors(sub.frame, R.cfg["rank"], per_slice=int(R.cfg.get("rank_cols", 0)) > 0)
+    sub.img = torch.zeros(R.frame.m, dtype=torch.float32, device=R.dev)
+    sub.graph = None
+    sub.pixels = sub.row_perm.to(torch.int64)
+    return sub
