@@ -169,6 +169,12 @@ lt_status lt_eval_pairs(lt_ctx* ctx, const float* pts, int64_t m, const float* v
  * lighting matrix, Sec. 3; the reference images of the experiments). */
 lt_status lt_bruteforce(lt_ctx* ctx, const float* pts, int64_t m, const float* vpls, int64_t n,
                         float d_min, float* img);
+/* Instrumentation (no counterpart in the paper): re-runs the brute force of the same
+ * points and VPLs without storing the image and returns in stats_host[4] the entries
+ * (m n), the shadow rays cast (entries with a positive unoccluded value), the grid
+ * cells visited and the box slab tests made.  Synchronous. */
+lt_status lt_bruteforce_stats(lt_ctx* ctx, const float* pts, int64_t m, const float* vpls, int64_t n,
+                              float d_min, int64_t* stats_host);
 
 /* ---- Step 1 (Sec. 3): light tree and conservative global light cut ---------- */
 /* Build the light tree of the VPLs into caller arrays sized for n. */

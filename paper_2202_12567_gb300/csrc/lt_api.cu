@@ -326,15 +326,19 @@ extern "C" lt_status lt_eval_pairs(lt_ctx* ctx, const float* pts, int64_t m, con
 constexpr int kBfThreads = 128;
 constexpr int kBfTile = 128;
 
+template <bool COUNT>
 __global__ void __launch_bounds__(kBfThreads) k_bruteforce(Grid g, const float4* __restrict__ pts, int64_t m,
                                                            const float4* __restrict__ vpls, int64_t n, float dmin2,
-                                                           float* __restrict__ img) {
+                                                           float* __restrict__ img,
+                                                           unsigned long long* __restrict__ stats) {
     __shared__ float4 tile[3][kBfTile];
     const int64_t i = blockIdx.x * (int64_t)kBfThreads + threadIdx.x;
     const bool live = i < m;
     PointRec P;
     if (live) P = load_rec(pts, m, i);
     float acc = 0.f;
+    WorkCount wc;
+    int rays = 0;
     for (int64_t j0 = 0; j0 < n; j0 += kBfTile) {
         const int cnt = (int)((n - j0) < kBfTile ? (n - j0) : kBfTile);
         __syncthreads();
@@ -350,11 +354,20 @@ __global__ void __launch_bounds__(kBfThreads) k_bruteforce(Grid g, const float4*
                 L.a = tile[0][t];
                 L.b = tile[1][t];
                 L.c = tile[2][t];
-                acc += entry_value(P, L, 1.f, dmin2, g);
+                acc += entry_value<COUNT>(P, L, 1.f, dmin2, g, &wc, &rays);
             }
         }
     }
-    if (live) img[i] = acc;
+    if (COUNT) {
+        if (live) {
+            atomicAdd(stats + 0, (unsigned long long)n);
+            atomicAdd(stats + 1, (unsigned long long)rays);
+            atomicAdd(stats + 2, (unsigned long long)wc.cells);
+            atomicAdd(stats + 3, (unsigned long long)wc.boxes);
+        }
+    } else if (live) {
+        img[i] = acc;
+    }
 }
 
 extern "C" lt_status lt_bruteforce(lt_ctx* ctx, const float* pts, int64_t m, const float* vpls, int64_t n,
@@ -363,9 +376,30 @@ extern "C" lt_status lt_bruteforce(lt_ctx* ctx, const float* pts, int64_t m, con
         return lt_fail(ctx, LT_EINVAL, "lt_bruteforce: bad arguments");
     if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_bruteforce: no scene uploaded");
     const int64_t blocks = (m + kBfThreads - 1) / kBfThreads;
-    k_bruteforce<<<(unsigned)blocks, kBfThreads, 0, ctx->stream>>>(ctx->grid, (const float4*)pts, m,
-                                                                  (const float4*)vpls, n, d_min * d_min, img);
+    k_bruteforce<false><<<(unsigned)blocks, kBfThreads, 0, ctx->stream>>>(
+        ctx->grid, (const float4*)pts, m, (const float4*)vpls, n, d_min * d_min, img, nullptr);
     LT_LAUNCH_CHECK(ctx, "k_bruteforce");
+    return LT_OK;
+}
+
+extern "C" lt_status lt_bruteforce_stats(lt_ctx* ctx, const float* pts, int64_t m, const float* vpls, int64_t n,
+                                         float d_min, int64_t* stats_host) {
+    if (!ctx || m <= 0 || n <= 0 || !pts || !vpls || !stats_host || !aligned16(pts) || !aligned16(vpls))
+        return lt_fail(ctx, LT_EINVAL, "lt_bruteforce_stats: bad arguments");
+    if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_bruteforce_stats: no scene uploaded");
+    cudaSetDevice(ctx->device);
+    lt_status st;
+    unsigned long long* stats = (unsigned long long*)lt_scratch(ctx, SCR_MISC, 256, &st);
+    if (!stats) return st;
+    LT_CUDA(ctx, cudaMemsetAsync(stats, 0, 4 * 8, ctx->stream));
+    const int64_t blocks = (m + kBfThreads - 1) / kBfThreads;
+    k_bruteforce<true><<<(unsigned)blocks, kBfThreads, 0, ctx->stream>>>(
+        ctx->grid, (const float4*)pts, m, (const float4*)vpls, n, d_min * d_min, nullptr, stats);
+    LT_LAUNCH_CHECK(ctx, "k_bruteforce<count>");
+    unsigned long long h[4];
+    LT_CUDA(ctx, cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 4; ++i) stats_host[i] = (int64_t)h[i];
     return LT_OK;
 }
 

@@ -265,49 +265,54 @@ __device__ inline bool seg_blocked(const Grid& g, float3 o, float3 e, WorkCount*
 }
 
 // ----------------------------------------------------------------- entry model
-// Phong lobe: cos a = R(wi) . wo = 2 (n.wi)(n.wo) - wi.wo.  The lobe raises cos a to
-// the exponent e (up to 100), which multiplies the relative rounding error of cos a
-// by e; so cos a - 1 is formed in double from the float inputs and the power is taken
-// as exp(e log1p(cos a - 1)).
+// Float pairs (hi, lo) holding a value as an unevaluated sum, from the error-free
+// transformations of Knuth (two-sum: the exact rounding error of a + b) and Dekker
+// (two-product: the exact rounding error of a b, here by one fma).
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// a . b of float3 as a float pair (error of order 2^-46 |a||b|)
+__device__ __forceinline__ F2 dot3_f2(float3 a, float3 b) {
+    const F2 p0 = two_prod(a.x, b.x), p1 = two_prod(a.y, b.y), p2 = two_prod(a.z, b.z);
+    const F2 s1 = two_sum(p0.hi, p1.hi);
+    const F2 s2 = two_sum(s1.hi, p2.hi);
+    return {s2.hi, __fadd_rn(__fadd_rn(__fadd_rn(p0.lo, p1.lo), __fadd_rn(p2.lo, s1.lo)), s2.lo)};
+}
+
+// Phong lobe: cos a = R(wi) . wo with R(wi) = 2 (n.wi) n - wi the mirrored incident
+// direction, so cos a - 1 = 2 (n.wi)(n.wo) - wi.wo - 1.  The lobe raises cos a to the
+// exponent e (up to 100), which multiplies the error of cos a - 1 by e, and near the
+// peak the terms cancel: they are carried as float pairs, so the cancellation is
+// exact and cos a - 1 is as accurate as a float can hold it.  The power is taken as
+// exp(e log1p(cos a - 1)).
 __device__ __forceinline__ float brdf(float alb, float gloss, float3 n, float3 wi, float3 wo) {
     if (!(gloss > 0.f)) return alb * kInvPi;
-    const double ni = (double)n.x * wi.x + (double)n.y * wi.y + (double)n.z * wi.z;
-    const double no = (double)n.x * wo.x + (double)n.y * wo.y + (double)n.z * wo.z;
-    const double io = (double)wi.x * wo.x + (double)wi.y * wo.y + (double)wi.z * wo.z;
-    const double cm1 = 2.0 * ni * no - io - 1.0;
-    const float lobe = cm1 > -1.0 ? expf(gloss * log1pf((float)cm1)) : 0.f;
+    const F2 ni = dot3_f2(n, wi), no = dot3_f2(n, wo), io = dot3_f2(wi, wo);
+    const F2 pp = two_prod(ni.hi, no.hi);  // (ni no) as a pair
+    const float plo = __fadd_rn(pp.lo, __fadd_rn(__fmul_rn(ni.hi, no.lo), __fmul_rn(ni.lo, no.hi)));
+    const F2 d1 = two_sum(__fmul_rn(2.f, pp.hi), -io.hi);                 // 2 ni no - io
+    const float l1 = __fadd_rn(d1.lo, __fsub_rn(__fmul_rn(2.f, plo), io.lo));
+    const F2 d2 = two_sum(d1.hi, -1.f);                                   // - 1
+    const float cm1 = __fadd_rn(d2.hi, __fadd_rn(d2.lo, l1));
+    const float lobe = cm1 > -1.f ? expf(gloss * log1pf(cm1)) : 0.f;
     return 0.5f * alb * kInvPi + 0.5f * alb * (gloss + 2.f) * (0.5f * kInvPi) * lobe;
 }
 
 struct PointRec {
     float4 a, b, c;   // [p albedo] [n gloss] [wo 0]
 };
-
-// Bytes of shared memory that staging the grid takes (0 if there is no grid).
-__host__ __device__ inline int grid_stage_bytes(const Grid& g) {
-    if (g.nb == 0) return 0;
-    const int cells = g.R * g.R * g.R + 1;
-    return ((cells + g.nlist) * 4 + 15) / 16 * 16 + g.nb * 24;
-}
-
-// Copy the grid into shared memory at `smem` (16-byte aligned) with the whole block
-// and return a Grid that points there.  Call with every thread of the block, then
-// __syncthreads() before use.
-__device__ inline Grid stage_grid(const Grid& g, char* smem) {
-    Grid s = g;
-    if (g.nb == 0) return s;
-    const int cells = g.R * g.R * g.R + 1;
-    int32_t* off = reinterpret_cast<int32_t*>(smem);
-    int32_t* lst = off + cells;
-    float* box = reinterpret_cast<float*>(smem + ((cells + g.nlist) * 4 + 15) / 16 * 16);
-    for (int i = threadIdx.x; i < cells; i += blockDim.x) off[i] = g.cell_off[i];
-    for (int i = threadIdx.x; i < g.nlist; i += blockDim.x) lst[i] = g.cell_box[i];
-    for (int i = threadIdx.x; i < g.nb * 6; i += blockDim.x) box[i] = g.box[i];
-    s.cell_off = off;
-    s.cell_box = lst;
-    s.box = box;
-    return s;
-}
 
 __device__ __forceinline__ PointRec load_rec(const float4* __restrict__ planes, int64_t count, int64_t i) {
     PointRec r;

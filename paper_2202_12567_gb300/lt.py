@@ -90,6 +90,7 @@ _SIGS = {
     "lt_shadow_test": (_i32, [_p, _p, _p, _i64, _p]),
     "lt_eval_pairs": (_i32, [_p, _p, _i64, _p, _i64, _p, _p, _p, _i64, _f32, _p]),
     "lt_bruteforce": (_i32, [_p, _p, _i64, _p, _i64, _f32, _p]),
+    "lt_bruteforce_stats": (_i32, [_p, _p, _i64, _p, _i64, _f32, _p]),
     "lt_build_tree": (_i32, [_p, _p, _i64, ctypes.POINTER(lt_tree)]),
     "lt_build_global_cut": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i64, _p, _p, _i64, _f32, _i32, _f32, _f32,
                                    _p, ctypes.POINTER(_i32)]),
@@ -248,6 +249,13 @@ def lt_bruteforce(ctx: Context, pts, vpls, d_min=0.01, out=None) -> torch.Tensor
     ctx._check("lt_bruteforce", ctx.lib.lt_bruteforce(ctx.h, _ptr(pts), m, _ptr(vpls), vpls.shape[1], d_min,
                                                       _ptr(img)))
     return img
+
+
+def lt_bruteforce_stats(ctx: Context, pts, vpls, d_min=0.01) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    ctx._check("lt_bruteforce_stats", ctx.lib.lt_bruteforce_stats(ctx.h, _ptr(pts), pts.shape[1], _ptr(vpls),
+                                                                  vpls.shape[1], d_min, ctypes.cast(out, _p)))
+    return dict(entries=out[0], rays=out[1], cells=out[2], boxes=out[3])
 
 
 class Tree:

@@ -109,6 +109,65 @@ def ab_compare(ctx: lt.Context, cfg: dict, theta, scene_seeds, mix: float = 0.8,
     return out
 
 
+def iso_error(ctx: lt.Context, cfg: dict, theta, scene_seeds, rates, target: float = 0.02, mix: float = 0.8,
+              timing_scene: int | None = None, replays: int = 10):
+    """The two pass-2 pdfs at equal error instead of equal sample count: for every
+    rate, the mean rel-RMSE over the held-out scenes of the frame with g (the paper)
+    and with the learned proposal; each form's iso rate is the lowest rate whose mean
+    is <= target, and its ms/frame is the median replay of the captured frame at that
+    rate on `timing_scene` (L2 flushed between replays)."""
+    from ltinputs import make_scene
+    rates = sorted(float(r) for r in rates)
+    top = dict(cfg, rate=rates[-1])
+    err = {"g": np.zeros(len(rates)), "learned": np.zeros(len(rates))}
+    for s in scene_seeds:
+        R = Renderer(make_scene(top, s), top, device=ctx.device, ctx=ctx).setup()
+        ref = R.bruteforce().double()
+        nref = float(torch.linalg.norm(ref))
+        for k, rate in enumerate(rates):
+            R.cfg["rate"] = rate
+            for form in ("g", "learned"):
+                prm = lt.params(R.cfg, proposal=theta if form == "learned" else None, mix=mix)
+                lt.lt_render_frame(ctx, R.frame, prm, R.cfg["frame_seed"], R.smp, R.uv, R.row_perm, R.img)
+                lt.lt_sync(ctx)
+                err[form][k] += float(torch.linalg.norm(R.img.double() - ref)) / nref / len(scene_seeds)
+        del R
+    out = dict(target=target, rates=rates, scenes=len(scene_seeds),
+               mean_rel_rmse={f: [round(float(x), 5) for x in v] for f, v in err.items()})
+    scene = make_scene(top, scene_seeds[0] if timing_scene is None else timing_scene)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    for form in ("g", "learned"):
+        ok = [k for k in range(len(rates)) if err[form][k] <= target]
+        if not ok:
+            out[form] = dict(iso_rate=None)
+            continue
+        rate = rates[ok[0]]
+        R = Renderer(scene, dict(top, rate=rate), device=ctx.device, ctx=ctx).setup()
+        g = lt.lt_frame_graph_capture(ctx, R.frame, lt.params(R.cfg, proposal=theta if form == "learned" else None,
+                                                              mix=mix), R.smp, R.uv, R.row_perm, R.img,
+                                      keep=(theta,))
+        for k in range(3):
+            lt.lt_frame_graph_launch(g, 9000 + k)
+        ms = []
+        for k in range(replays):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            lt.lt_frame_graph_launch(g, 9100 + k)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        ref = R.bruteforce().double()
+        lt.lt_frame_graph_launch(g, R.cfg["frame_seed"])
+        lt.lt_sync(ctx)
+        rel = float(torch.linalg.norm(R.img.double() - ref) / torch.linalg.norm(ref))
+        out[form] = dict(iso_rate=rate, ms_per_frame=round(float(np.median(ms)), 4),
+                         rel_rmse_timing_scene=round(rel, 5), entries=int(R.smp.cnt.sum()))
+        g.close()
+        del R
+    return out
+
+
 def main():
     from ltinputs import get_config
     ap = argparse.ArgumentParser()

@@ -7,6 +7,8 @@ owns the tensors.
 """
 from __future__ import annotations
 
+import time
+
 import numpy as np
 import torch
 
@@ -46,7 +48,17 @@ class Renderer:
         given (e.g. from another implementation) instead of being computed."""
         cfg = self.cfg
         ctx = self.ctx
+        times = {}
+        mark = [time.perf_counter()]
+
+        def lap(name):  # host time of the stage just finished (the stream is synchronised)
+            torch.cuda.synchronize(self.dev)
+            now = time.perf_counter()
+            times[name] = round((now - mark[0]) * 1e3, 3)
+            mark[0] = now
+
         self.tree = lt.lt_build_tree(ctx, self.vpls)
+        lap("light_tree")
         if cut is None:
             rows = torch.from_numpy(test_rows(self.scene.width, self.scene.height).astype(np.int32)).to(self.dev)
             cut = lt.lt_build_global_cut(ctx, self.tree, self.pts, self.vpls, rows, cfg["eps_cut"], cfg["max_cut"],
@@ -54,7 +66,9 @@ class Renderer:
         else:
             cut = torch.as_tensor(np.asarray(cut), dtype=torch.int32).to(self.dev)
         self.cut = cut
+        lap("global_cut")
         forest, level_off, level_nodes, H = lt.lt_cut_forest(ctx, self.tree, cut)
+        lap("cut_forest")
         if row_perm is None and cfg.get("slicing", "kmeans") == "split6d":  # the paper's recursive split
             row_perm, slice_off = lt.lt_make_slices_split(ctx, self.pts, cfg["slice_size"],
                                                           cfg["slice_feature_normal_weight"])
@@ -65,12 +79,15 @@ class Renderer:
             row_perm = torch.as_tensor(np.asarray(row_perm), dtype=torch.int32).to(self.dev)
             slice_off = torch.as_tensor(np.asarray(slice_off), dtype=torch.int32).to(self.dev)
         self.row_perm, self.slice_off = row_perm, slice_off
+        lap("slices")
         self.pts_s = lt.lt_permute_points(ctx, self.pts, row_perm)
         self.frame = lt.Frame(self.pts_s, self.vpls, slice_off, self.tree, cut, forest, level_off, level_nodes, H)
         self.smp = lt.Samples(self.frame, cfg["rate"], cfg["rate1"])
         self.uv = lt.Factors(self.frame, cfg["rank"], per_slice=int(cfg.get("rank_cols", 0)) > 0)
         self.img = torch.zeros(self.frame.m, dtype=torch.float32, device=self.dev)
         lt.lt_sync(ctx)
+        lap("points_and_buffers")
+        self.setup_ms = times
         return self
 
     # ---------------------------------------------------------------- frame stages
