@@ -23,7 +23,8 @@ For one slice with m' rows the global cut is coarsened from sparse samples:
        eps(f)  = max_{i in zeta_f} | V_q(i) - V_p(i) I_q / I_p |        (Sec. 4)
        cost(f) = eps(f) + cost(q),   cost = 0 on the global cut         (Eq. 2)
    and f replaces a, b when cost(f) < tau * S_hat, with V_f = V_p I_f / I_p (no new
-   rays).  A pair's decision depends only on its own subtree, so the order in which
+   rays).  In a dark slice (S_hat = 0) the bound is zero and a pair of cost exactly
+   zero merges (see merges()).  A pair's decision depends only on its own subtree, so the order in which
    pairs are tested does not change the result; the oracle tests in rounds.
 4. Output: the coarsened cut in leaf order (the slice's columns), the observed
    entries of each column and g(c) = max - min of them (Sec. 5, Eq. for g).  A
@@ -138,6 +139,14 @@ def forest_heights(forest: Forest) -> np.ndarray:
     return height
 
 
+def merges(cost: float, thr: float, s_hat: float) -> bool:
+    """The Sec. 4 test: merge while the cost is below the bound tau * S_hat.  In a
+    dark slice (S_hat = 0, every pass-1 entry zero) the bound is zero; it is read as
+    met by a pair whose cost is exactly zero, whose entries agree on every sampled
+    row, so that the slice coarsens as far as its samples cannot tell lights apart."""
+    return cost < thr or (s_hat == 0.0 and cost == 0.0)
+
+
 def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int, row0: int,
                   m_s: int, rate1: float, tau: float, seed: int, d_min=0.01,
                   order_rng: np.random.Generator | None = None, target: int | None = None) -> Pass1Slice:
@@ -222,7 +231,7 @@ def coarsen_slice(tree: LightTree, forest: Forest, points_s, vpls, boxes, s: int
                 order_rng.shuffle(todo)
             for f in todo:
                 t = test_pair(f)
-                merged = t["cost"] < thr
+                merged = merges(t["cost"], thr, s_hat)
                 log.append((f, t["eps"], t["cost"], thr, bool(merged), t["p"], t["q"], t["rf"],
                             t["full"][t["p"]], t["full"][t["q"]]))
                 if merged:

@@ -6,7 +6,8 @@
 //    slices: sibling pairs are laid out as the union zeta_f = zeta_a U zeta_b (one
 //    thread per small pair, one CTA per big pair), the entries missing from either
 //    child are queued and evaluated one shadow ray per thread, and each pair merges
-//    when cost = eps + cost(q) < tau * S_hat, eps = max |V_q - V_p I_q / I_p|.
+//    when cost = eps + cost(q) < tau * S_hat, eps = max |V_q - V_p I_q / I_p| (in a dark
+//    slice, S_hat = 0, when the cost is exactly zero).
 //  * Pass 2 (Sec. 5, Eq. 3): per slice one cluster of eight CTAs draws (column from
 //    the integer CDF of g or of given weights, row uniform) in rounds, keeps the
 //    first occurrence of every new entry in draw order, and stops at
@@ -119,7 +120,7 @@ struct P1Store {
 struct P1Work {
     int64_t* kpfx;     // [S+1] prefix over slices of the initial entry counts
     float* leafmean;   // [S][C] mean of each cut node's initial entries
-    float* thr;        // [S] tau * S_hat
+    float* thr;        // [S] tau * S_hat (-1 in a dark slice, S_hat = 0)
     int64_t* mcount;   // [Hmax] queued missing entries per level
     int64_t* bcount;   // [Hmax] big pairs per level
     int64_t* mdst;     // [mcap] flat value index (v0 or v1) of a missing entry
@@ -252,7 +253,10 @@ __global__ void k_p1_leafmean(lt_frame F, P1Plan pl, P1Store st, float* leafmean
     }
 }
 
-// tau * S_hat per slice, S_hat = sum_c mean(V_c) (fixed reduction order)
+// tau * S_hat per slice, S_hat = sum_c mean(V_c) (fixed reduction order).  A dark
+// slice (S_hat = 0: every pass-1 entry is zero) gets -1: its relative bound is zero,
+// and it is read as met by a pair whose cost is exactly zero (the samples cannot
+// tell the two lights apart), so such a slice coarsens as far as its entries agree.
 __global__ void k_p1_thr(lt_frame F, const float* __restrict__ leafmean, float tau, float* thr) {
     __shared__ float red[32];
     const int s = blockIdx.x;
@@ -264,7 +268,7 @@ __global__ void k_p1_thr(lt_frame F, const float* __restrict__ leafmean, float t
     if (threadIdx.x == 0) {
         float t = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        thr[s] = tau * t;
+        thr[s] = t > 0.f ? tau * t : -1.f;
     }
 }
 
@@ -570,7 +574,8 @@ __device__ __forceinline__ void decide_pair(const lt_frame& F, const P1Plan& pl,
     int32_t* state = pl.state + (int64_t)pc.s * NF;
     const int q = p_is_a ? pc.b : pc.a;
     const float cf = e_max + cost[q];
-    const bool merge = cf < thr[pc.s];
+    const float th = thr[pc.s];
+    const bool merge = th < 0.f ? cf == 0.f : cf < th;  // th < 0: a dark slice
     const int nf = pl.cnt[(int64_t)pc.s * NF + pc.f];
     if (merge) {
         const float rfp = __fdiv_rn(If, p_is_a ? Ia : Ib);

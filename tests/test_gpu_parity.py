@@ -294,6 +294,39 @@ def test_pass1_coarsened_cut_and_entries(tiny_gpu):
     assert n_exact >= len(p1) - 1
 
 
+def test_pass1_dark_slice_matches_oracle(lt, tiny):
+    """Zero albedo on the points of two slices (every entry of them zero, S_hat = 0):
+    the kernels coarsen them to the forest root as the oracle does, and the other
+    slices keep the oracle's cuts."""
+    from paper_2202_12567_gb300.renderer import Renderer
+    cfg, sc, st = tiny
+    R = Renderer(sc, cfg, device=0).setup(cut=st["cut"], row_perm=st["row_perm"], slice_off=st["slice_off"])
+    dark = dict(st, pts_s=st["pts_s"].copy())
+    off = st["slice_off"]
+    for s in (2, 5):
+        a, b = int(off[s]), int(off[s + 1])
+        dark["pts_s"][0, a:b, 3] = 0.0
+        R.pts_s[0, a:b, 3] = 0.0
+    seed = cfg["frame_seed"]
+    R.pass1(seed)
+    lt.lt_sync(R.ctx)
+    fo = st["forest"]
+    for s in range(R.frame.S):
+        rows, cols, vals, col_node, g = R.smp.slice(s)
+        o = pipeline.run_slice(dark, sc, cfg, s, seed).p1
+        if s in (2, 5):
+            assert o.s_hat == 0.0 and np.array_equal(o.col_node, fo.node[fo.parent == -1])
+            assert np.array_equal(col_node, o.col_node), f"dark slice {s}"
+            assert np.all(vals == 0.0)
+        elif not np.array_equal(col_node, o.col_node):
+            margins = [abs(cf - thr) / max(thr, 1e-30) for (_, _, cf, thr, *_rest) in o.log]
+            assert min(margins) < 1e-4, f"slice {s}: coarsened cut differs without a near tie"
+    img = R.render(seed).cpu().numpy()
+    perm = st["row_perm"]
+    for s in (2, 5):
+        assert np.all(img[perm[off[s]:off[s + 1]]] == 0.0)
+
+
 def _load_samples(lt, R, p1_per_slice):
     """Write pass-1 entries (rows, cols, vals, col_node, g) of every slice into R.smp."""
     smp = R.smp

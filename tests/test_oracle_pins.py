@@ -288,11 +288,31 @@ def test_pass1_eps_identity_and_cost_recursion(tiny_setup):
                                        np.full(rf.size, tree_mod.node_scale(tr, sc.vpls, [t])[0]), sc.boxes)
             np.testing.assert_allclose(vx, ref, rtol=1e-12, atol=0)
         assert abs(cf - (eps + cost.get(q, 0.0))) <= 1e-15 + 1e-12 * cf
-        assert merged == (cf < thr)
+        assert thr > 0 and merged == (cf < thr)
         if merged:
             cost[f] = cf
             n_merged += 1
     assert n_merged > 0
+
+
+@pytest.mark.parametrize("tau", [None, 0.0])
+def test_pass1_dark_slice_coarsens_to_the_root(tiny_setup, tau):
+    """A slice whose shading points have zero albedo: every entry is zero, so S_hat = 0
+    and every pair's cost is zero; the zero bound is read as met by a zero cost, so
+    every pair merges (with any tau) and the coarsened cut is the forest's root."""
+    cfg, sc, st = tiny_setup
+    s = 3
+    a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
+    dark = dict(st, pts_s=st["pts_s"].copy())
+    dark["pts_s"][0, a:b, 3] = 0.0
+    res = _run_p1(cfg, sc, dark, s, tau=tau)
+    fo = st["forest"]
+    assert res.s_hat == 0.0 and len(res.log) == fo.C - 1
+    assert all(merged for (_, _, _, _, merged, *_rest) in res.log)
+    assert np.array_equal(res.col_node, fo.node[fo.parent == -1])
+    assert np.all(res.vals == 0.0) and np.all(res.g == 0.0)
+    # the same slice lit keeps columns apart
+    assert _run_p1(cfg, sc, st, s).col_node.size > 1
 
 
 def test_pass1_tau_zero_never_merges(tiny_setup):
