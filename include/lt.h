@@ -278,6 +278,18 @@ lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, const lt_sa
  * line's Gram again in float64 and solves it in float64). */
 lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
                       float lam_rel, uint64_t seed, lt_factors* uv);
+/* The tensor-core contraction of one ALS half-step alone, a check of the Gram
+ * matrices of the completion (Sec. 5; lt_complete with als_form 1).  Side 0: every
+ * row i of every slice gets G_i = sum_j v_j v_j^T and b_i = sum_j A_ij v_j over its
+ * observed entries (i, j), v_j the rows of uv->V; side 1: every column j gets the
+ * same over its entries with the rows u_i of uv->U.  Written to `gram` (device,
+ * float32, caller-allocated) at line L = the slice-ordered row (side 0: m lines) or
+ * s C + j (side 1: S C lines), stride r (r + 3) / 2: the packed lower triangle of G
+ * (element (a, c), c <= a, at a (a + 1) / 2 + c), then b.  Lines past n'_s are not
+ * written.  LT_EINVAL unless 1 <= uv->r <= 16 and uv->rank is NULL. */
+lt_status lt_als_gram(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv, int32_t side,
+                      float* gram);
+
 /* Lines (rows of U or columns of V, summed over every half-step) that the last
  * lt_complete of the context solved in float64 because their float32 pivots failed
  * the check above; their Gram is formed again in float64 from the float32 factors.
@@ -344,13 +356,15 @@ lt_status lt_expand_rgb(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, c
 
 /* ---- Launch tuning (no counterpart in the paper) ---------------------------
  * Launch shapes the library lets a caller tune per workload; they change no result
- * beyond the float summation order of the ALS Gram (als_lane_entries).  The values
+ * beyond the float rounding of the ALS Gram (als_lane_entries, als_form).  The values
  * apply to later calls and to later graph captures of the context. */
 typedef struct {
     int32_t eval_ctas_per_sm;   /* entry evaluation: persistent CTAs of 128 threads per SM (1..64), 16 */
     int32_t ray_ctas_per_sm;    /* pass-1 shadow-ray kernels: the same (1..64), 16 */
     int32_t als_lane_entries;   /* ALS (r <= 16): a line gets 2^g lanes so that a lane holds at most about
                                    this many of its entries (16..1024), 96 */
+    int32_t als_form;           /* ALS (r <= 16): 1 = Gram and right-hand side as dense masked products on
+                                   the tensor cores (tcgen05), 0 = lane-group SIMT kernel; 0 */
 } lt_tuning;
 lt_status lt_get_tuning(const lt_ctx* ctx, lt_tuning* t);
 /* LT_EINVAL (and no change) if a value is out of range. */

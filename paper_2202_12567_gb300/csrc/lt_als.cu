@@ -23,12 +23,13 @@
 
 #include "lt_internal.cuh"
 #include "lt_omega.cuh"
+#include "lt_als_common.cuh"
+#include "lt_als_tc.cuh"
 
 using namespace ltk;
 
 namespace {
 
-constexpr float kPivotRatio = 1e-6f;
 
 
 // Group-size classes of a line: class g gives a line of L entries G = 2^g lanes, so
@@ -711,84 +712,6 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
 // Lines whose pivots fail the check go to a queue; a second kernel forms their
 // Gram again in float64 (products of the float32 factors are exact in float64) and
 // solves it in float64, so an ill-conditioned line carries no float32 rounding.
-template <int RP>
-struct AlsQueue {
-    int32_t* count;     // [1] lines queued by this half-step
-    int64_t* dst;       // [cap] output row offset (floats) of each queued line
-    int64_t* slot;      // [cap] first slot of the line's first lane stream in the sliced layout
-    int64_t* src;       // [cap] offset (floats) in the source factors of the slice's rows
-    int32_t* len;       // [cap] entries of the line
-    int32_t* grp;       // [cap] lanes G of the line (entry e is entry e / G of stream e % G)
-    int32_t* rank;      // [cap] rank of each queued line
-    int64_t cap;
-    int32_t* status;    // device status word (LT_ELIMIT when the queue overflows)
-};
-
-// Cholesky solve of (G + lam I) u = b in place (u returned in b); rows i >= r are
-// identity rows with b_i = 0.  Returns false when `check` and the float pivots are
-// not acceptable (a non-positive pivot or min/max pivot^2 < kPivotRatio).
-template <int RP, typename T>
-__device__ __forceinline__ bool chol_solve(T (&a)[RP * (RP + 1) / 2], T (&b)[RP], int r, float lam_rel, bool check) {
-    T tr = T(0);
-#pragma unroll
-    for (int i = 0; i < RP; ++i) tr += a[i * (i + 1) / 2 + i];
-    if (!(tr > T(0))) {  // no observed entry (or all-zero factors): zero factor
-#pragma unroll
-        for (int i = 0; i < RP; ++i) b[i] = T(0);
-        return true;
-    }
-    const T lam = (T)lam_rel * tr / (T)r;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {
-        if (i < r) {
-            a[i * (i + 1) / 2 + i] += lam;
-        } else {
-#pragma unroll
-            for (int j = 0; j <= i; ++j) a[i * (i + 1) / 2 + j] = (j == i) ? T(1) : T(0);
-            b[i] = T(0);
-        }
-    }
-    T dmin = T(3.0e38), dmax = T(0);
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < RP; ++j) {
-        T d = a[j * (j + 1) / 2 + j];
-#pragma unroll
-        for (int k = 0; k < j; ++k) d -= a[j * (j + 1) / 2 + k] * a[j * (j + 1) / 2 + k];
-        if (j < r) {
-            ok &= d > T(0);
-            dmin = d < dmin ? d : dmin;
-            dmax = d > dmax ? d : dmax;
-        }
-        const T ljj = sqrt(d > T(0) ? d : T(1));
-        const T inv = T(1) / ljj;
-        a[j * (j + 1) / 2 + j] = ljj;
-#pragma unroll
-        for (int i = j + 1; i < RP; ++i) {
-            T t = a[i * (i + 1) / 2 + j];
-#pragma unroll
-            for (int k = 0; k < j; ++k) t -= a[i * (i + 1) / 2 + k] * a[j * (j + 1) / 2 + k];
-            a[i * (i + 1) / 2 + j] = t * inv;
-        }
-    }
-    if (check && (!ok || dmin < (T)kPivotRatio * dmax)) return false;
-#pragma unroll
-    for (int i = 0; i < RP; ++i) {  // L y = b
-        T t = b[i];
-#pragma unroll
-        for (int k = 0; k < i; ++k) t -= a[i * (i + 1) / 2 + k] * b[k];
-        b[i] = t / a[i * (i + 1) / 2 + i];
-    }
-#pragma unroll
-    for (int i = RP - 1; i >= 0; --i) {  // L^T x = y
-        T t = b[i];
-#pragma unroll
-        for (int k = i + 1; k < RP; ++k) t -= a[k * (k + 1) / 2 + i] * b[k];
-        b[i] = t / a[i * (i + 1) / 2 + i];
-    }
-    return true;
-}
-
 // A staged factor row is RP floats (RP/4 16-byte slots).  Slot q of row j is stored
 // at slot q ^ h(j) so that the rows read by one quarter-warp (random j) spread over
 // all eight 16-byte bank groups of a 128-byte shared-memory wavefront.
@@ -1086,10 +1009,16 @@ __global__ void __launch_bounds__(128) k_als_retry(AlsQueue<RP> q, Omega om, boo
         for (int e0 = 0; e0 < len; e0 += 32) {
             const int e = e0 + lane;
             if (e < len) {
-                const int u = e % G, kk = e / G;
-                const int64_t pos = slot + 4 * u + 128 * (kk >> 2) + (kk & 3);
-                const int j = sidx[pos];
-                av[w][lane] = sval[pos];
+                int j;
+                if (G > 0) {  // sliced layout
+                    const int u = e % G, kk = e / G;
+                    const int64_t pos = slot + 4 * u + 128 * (kk >> 2) + (kk & 3);
+                    j = sidx[pos];
+                    av[w][lane] = sval[pos];
+                } else {      // CSR / CSC
+                    j = (rows_side ? om.cidx : om.ridx)[slot + e];
+                    av[w][lane] = (rows_side ? om.cval : om.rval)[slot + e];
+                }
 #pragma unroll
                 for (int c = 0; c < RP; ++c) xs[w][lane][c] = c < r ? src[(int64_t)j * R + c] : 0.f;
             }
@@ -1275,12 +1204,15 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const int64_t mr = std::max(f->max_rows, 1);
     const int R = uv->r;            // stride of the factor rows, the largest rank
     const int32_t* rk = uv->rank;   // per-slice ranks (NULL: R for every slice)
-    // the lane-group ALS takes slices of rank <= 16 (sliced layout), the warp-group
-    // ALS the others (CSR / CSC); with per-slice ranks above 16 both run
+    // Slices of rank <= 16 go to the tensor-core form (CSR / CSC) or the lane-group
+    // SIMT kernel (sliced layout), as tuned; the warp-group ALS takes the others
+    // (CSR / CSC); with per-slice ranks above 16 two of them run.
+    const bool low = R <= 16 || rk != nullptr;
+    const bool tc = low && ctx->tune.als_form == 1;
     Omega om;
-    lt_status st = omega_build(ctx, f, smp, E, R <= 16 || rk != nullptr, R > 16, &om);
+    lt_status st = omega_build(ctx, f, smp, E, low && !tc, R > 16 || tc, &om);
     if (st != LT_OK) return st;
-    const int RP = R <= 8 ? 8 : 16;  // lane-group kernel for ranks up to RP
+    const int RP = R <= 8 ? 8 : 16;  // the low-rank kernels cover ranks up to RP
     // per half-step retry counters and the float64 count
     const int nq = std::max(1, 2 * iters);
     char* sp = (char*)lt_scratch(ctx, SCR_ALS, (size_t)(nq + 64) * 4 + 256, &st);
@@ -1299,7 +1231,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const int64_t cap = std::min<int64_t>(std::max<int64_t>(f->m, (int64_t)S * C), 1 << 18);
     int64_t *qdst = nullptr, *qslot = nullptr, *qsrc = nullptr;
     int32_t *qlen = nullptr, *qgrp = nullptr, *qrank = nullptr;
-    if (om.sell) {
+    if (low) {
         const size_t a8 = ((size_t)cap * 8 + 255) & ~(size_t)255, a4 = ((size_t)cap * 4 + 255) & ~(size_t)255;
         char* qp = (char*)lt_scratch(ctx, SCR_GRAM, 3 * a8 + 3 * a4, &st);
         if (!qp) return st;
@@ -1309,6 +1241,8 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         qlen = (int32_t*)(qp + 3 * a8);
         qgrp = (int32_t*)(qp + 3 * a8 + a4);
         qrank = (int32_t*)(qp + 3 * a8 + 2 * a4);
+    }
+    if (om.sell) {
         if (RP == 8)
             LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
         else
@@ -1320,15 +1254,32 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const size_t hbudget = (size_t)210 * 1024 > hstat ? (size_t)210 * 1024 - hstat : 0;
     const int hstage_rows = (int)std::min<size_t>(hbudget / (33 * 4), (size_t)1 << 20);
     const size_t hdyn = (size_t)hstage_rows * 33 * 4;
-    if (om.csr)
+    if (R > 16)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hdyn));
+    TcPlan tcp{};
+    if (tc) {
+        st = als_tc_plan(ctx, f, smp, om, E, R, rk, RP, 2 * iters, &tcp);
+        if (st != LT_OK) return st;
+    }
     for (int it = 0; it < iters; ++it) {
         for (int side = 0; side < 2; ++side) {
             const bool rows = side == 0;
             const float* fin = rows ? uv->V : uv->U;
             float* fout = rows ? uv->U : uv->V;
             int32_t* cnt = qcount + 2 * it + side;
-            if (om.sell && RP == 8) {
+            if (tc) {
+                TcQueue tq{cnt, qdst, qslot, qsrc, qlen, qgrp, qrank, cap, ctx->d_status};
+                st = als_tc_half(ctx, f, smp, om, R, rk, rows, fin, fout, lam_rel, tcp, 2 * it + side, tq, nullptr);
+                if (st != LT_OK) return st;
+                if (RP == 8) {
+                    AlsQueue<8> q{cnt, qdst, qslot, qsrc, qlen, qgrp, qrank, cap, ctx->d_status};
+                    k_als_retry<8><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
+                } else {
+                    AlsQueue<16> q{cnt, qdst, qslot, qsrc, qlen, qgrp, qrank, cap, ctx->d_status};
+                    k_als_retry<16><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
+                }
+                LT_LAUNCH_CHECK(ctx, "k_als_retry");
+            } else if (om.sell && RP == 8) {
                 AlsQueue<8> q{cnt, qdst, qslot, qsrc, qlen, qgrp, qrank, cap, ctx->d_status};
                 k_als_line<8><<<nsm, 256, dyn, ctx->stream>>>(*f, *smp, om, R, rk, rows, fin, fout, lam_rel, q,
                                                               stage_rows);
@@ -1343,7 +1294,7 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
                 k_als_retry<16><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
                 LT_LAUNCH_CHECK(ctx, "k_als_retry");
             }
-            if (om.csr) {
+            if (R > 16) {
                 k_als_half<32><<<dim3(P, S), 32 * als_warps<32>(), hdyn, ctx->stream>>>(
                     *f, *smp, om, R, rk, lam_rel, rows, fin, fout, n64, hstage_rows);
                 LT_LAUNCH_CHECK(ctx, "k_als_half");
@@ -1351,6 +1302,27 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         }
     }
     return LT_OK;
+}
+
+extern "C" lt_status lt_als_gram(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,
+                                 int32_t side, float* gram) {
+    if (!ctx || !frame_ok2(f) || !smp || !smp->key || !smp->val || !smp->off || !smp->cnt || !smp->ncol || !uv ||
+        !uv->U || !uv->V || uv->r < 1 || uv->r > 16 || uv->rank || (side != 0 && side != 1) || !gram)
+        return lt_fail(ctx, LT_EINVAL, "lt_als_gram: bad arguments");
+    cudaSetDevice(ctx->device);
+    int64_t E = 0;
+    LT_CUDA(ctx, cudaMemcpyAsync(&E, smp->off + f->S, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    Omega om;
+    lt_status st = omega_build(ctx, f, smp, E, false, true, &om);
+    if (st != LT_OK) return st;
+    const int R = uv->r, RP = R <= 8 ? 8 : 16;
+    TcPlan tcp{};
+    st = als_tc_plan(ctx, f, smp, om, E, R, nullptr, RP, 1, &tcp);
+    if (st != LT_OK) return st;
+    const TcQueue none{};
+    return als_tc_half(ctx, f, smp, om, R, nullptr, side == 0, side == 0 ? uv->V : uv->U, nullptr, 0.f, tcp, 0, none,
+                       gram);
 }
 
 extern "C" lt_status lt_complete_fp64_lines(lt_ctx* ctx, int64_t* count_host) {

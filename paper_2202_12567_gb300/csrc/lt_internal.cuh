@@ -443,6 +443,8 @@ enum ScratchSlot {
     SCR_FRAME_PROP,     // features, groups, logits and weights of a frame's proposal
     SCR_P2_CDF,         // pass-2 integer CDF of every slice
     SCR_ADM,            // second X buffer, U, Lambda, V and Pi of the ADM completion
+    SCR_TC_PLAN,        // tensor-core ALS: per-slice prefixes, scales and tile counters
+    SCR_TC_IMG,         // tensor-core ALS: W / X images of the source factor rows
     SCR_NSLOTS
 };
 
@@ -476,7 +478,7 @@ struct lt_ctx {
     const uint64_t* seed_dev = nullptr;    // device seed word of the graph being captured
     std::vector<void*> retired;            // scratch that live graphs may still reference
     int graphs = 0;                        // graphs alive on this context
-    lt_tuning tune{16, 16, 96};            // launch tuning (lt_set_tuning)
+    lt_tuning tune{16, 16, 96, 0};            // launch tuning (lt_set_tuning)
     int64_t scratch_limit = 0;             // bytes of scratch the context may hold (0: no limit)
 };
 

@@ -73,7 +73,8 @@ MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 32, 64, 10497
 
 
 class lt_tuning(ctypes.Structure):
-    _fields_ = [("eval_ctas_per_sm", _i32), ("ray_ctas_per_sm", _i32), ("als_lane_entries", _i32)]
+    _fields_ = [("eval_ctas_per_sm", _i32), ("ray_ctas_per_sm", _i32), ("als_lane_entries", _i32),
+                ("als_form", _i32)]
 
 
 _SIGS = {
@@ -96,6 +97,8 @@ _SIGS = {
                                    _p, ctypes.POINTER(_i32)]),
     "lt_cut_errors": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i64, _p, _p, _i64, _p, _i32, _f32, _p]),
     "lt_complete_fp64_lines": (_i32, [_p, ctypes.POINTER(_i64)]),
+    "lt_als_gram": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), ctypes.POINTER(lt_factors),
+                           _i32, _p]),
     "lt_cut_forest": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i32, _p, _p, _i32, _p, ctypes.POINTER(_i32)]),
     "lt_make_slices": (_i32, [_p, _p, _i64, _i32, _i32, _f32, _p, _p]),
     "lt_permute_points": (_i32, [_p, _p, _i64, _p, _p]),
@@ -503,6 +506,18 @@ def lt_eval_stats(ctx: Context, frame: Frame, smp: Samples, d_min) -> dict:
 def lt_complete(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, lam_rel, seed):
     ctx._check("lt_complete", ctx.lib.lt_complete(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
                                                   iters, lam_rel, seed, ctypes.byref(uv.struct())))
+
+
+def lt_als_gram(ctx: Context, frame: Frame, smp: Samples, uv: Factors, side: int):
+    """Gram matrices and right-hand sides of one ALS half-step from the tensor-core
+    contraction: [lines][r (r + 3) / 2] float32 (side 0: m slice-ordered rows, side 1:
+    S C columns; lines past n'_s stay NaN)."""
+    r = uv.r
+    lines = frame.m if side == 0 else frame.S * frame.C
+    out = torch.full((lines, r * (r + 3) // 2), float("nan"), dtype=torch.float32, device=uv.U.device)
+    ctx._check("lt_als_gram", ctx.lib.lt_als_gram(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
+                                                  ctypes.byref(uv.struct()), int(side), _ptr(out)))
+    return out
 
 
 def lt_complete_fp64_lines(ctx: Context) -> int:

@@ -114,15 +114,18 @@ def _thin_row_slices(rng, S, m_s, n_s, r, thin_every, k_thin, k_full):
     return out
 
 
+@pytest.mark.parametrize("form", [1, 0])
 @pytest.mark.parametrize("r", [8, 16])
-def test_als_float64_retry_on_rank_deficient_rows(r):
+def test_als_float64_retry_on_rank_deficient_rows(r, form):
     """Rows with fewer entries than the rank and a ridge of 1e-9 fail the float32
-    pivot check; the float64 pass solves them and the result matches the oracle."""
+    pivot check; the float64 pass solves them and the result matches the oracle
+    (both forms of the half-step: tensor cores and lane-group SIMT)."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_2202_12567_gb300 import lt
     lt.load()
     ctx = lt.Context(0)
+    lt.lt_set_tuning(ctx, als_form=form)
     S, m_s, n_s, iters, lam, seed = 3, 200, 3 * r + 16, 4, 1e-9, 11
     thin_every, k_thin, k_full = 5, r // 2, 3 * r + 4
     entries = _thin_row_slices(np.random.default_rng(r), S, m_s, n_s, r, thin_every, k_thin, k_full)
