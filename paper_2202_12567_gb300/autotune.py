@@ -26,6 +26,7 @@ CANDIDATES = {
     "eval_ctas_per_sm": ([4, 8, 16, 32], "eval"),
     "ray_ctas_per_sm": ([4, 8, 16, 32], "pass1"),
     "als_lane_entries": ([48, 64, 96, 128, 192], "complete"),
+    "als_form": ([0, 1], "complete"),   # lane-group SIMT Gram or the tensor-core (tcgen05) Gram
 }
 
 

@@ -23,12 +23,15 @@ def R():
 def test_tuning_round_trip_and_validation(R):
     from paper_2202_12567_gb300 import lt
     t0 = lt.lt_get_tuning(R.ctx)
-    assert t0 == dict(eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96)
+    assert t0 == dict(eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0)
     lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=4)
     assert lt.lt_get_tuning(R.ctx)["eval_ctas_per_sm"] == 4
     with pytest.raises(lt.LtError):
         lt.lt_set_tuning(R.ctx, als_lane_entries=8)
     assert lt.lt_get_tuning(R.ctx)["als_lane_entries"] == 96
+    with pytest.raises(lt.LtError):
+        lt.lt_set_tuning(R.ctx, als_form=2)
+    assert lt.lt_get_tuning(R.ctx)["als_form"] == 0
     lt.lt_set_tuning(R.ctx, **t0)
 
 
@@ -41,7 +44,11 @@ def test_launch_shapes_do_not_change_results(R):
     img = R.render_frame(seed=5)
     rel = float(torch.linalg.norm(img.double() - base.double()) / torch.linalg.norm(base.double()))
     assert rel < 1e-5
-    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96)
+    lt.lt_set_tuning(R.ctx, als_form=1)  # tensor-core Gram: split fp16 operands, fp32 accumulation
+    img = R.render_frame(seed=5)
+    rel = float(torch.linalg.norm(img.double() - base.double()) / torch.linalg.norm(base.double()))
+    assert rel < 1e-3  # the completion tolerance: another summation order over 10 sweeps
+    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0)
 
 
 def test_autotuner_picks_candidates_and_caches(R, tmp_path):
@@ -52,7 +59,7 @@ def test_autotuner_picks_candidates_and_caches(R, tmp_path):
     for name, (cands, _) in autotune.CANDIDATES.items():
         assert values[name] in cands
     assert lt.lt_get_tuning(R.ctx) == values
-    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96)
+    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0)
     key2, values2, cached2 = autotune.apply(R, "room64_vpl1k_2box", path=path)
     assert cached2 and key2 == key and values2 == values and lt.lt_get_tuning(R.ctx) == values
     assert key in json.load(open(path))
