@@ -365,6 +365,9 @@ typedef struct {
                                    this many of its entries (16..1024), 96 */
     int32_t als_form;           /* ALS (r <= 16): 1 = Gram and right-hand side as dense masked products on
                                    the tensor cores (tcgen05), 0 = lane-group SIMT kernel; 0 */
+    int32_t p1_form;            /* pass-1 forest levels: 1 = one persistent cooperative launch with grid-wide
+                                   barriers between the steps of a level, 0 = one launch per step and
+                                   level; 0 (the same results either way) */
 } lt_tuning;
 lt_status lt_get_tuning(const lt_ctx* ctx, lt_tuning* t);
 /* LT_EINVAL (and no change) if a value is out of range. */

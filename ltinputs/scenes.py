@@ -41,6 +41,8 @@ from __future__ import annotations
 import dataclasses
 import math
 
+import os
+
 import numpy as np
 
 CAMERA_POS = np.array([0.5, 0.5, -1.35])
@@ -205,12 +207,37 @@ def _materials(n_faces: int, glossy_frac: float, rng: np.random.Generator):
     return albedo, gloss
 
 
-def _nearest_hit(org: np.ndarray, d: np.ndarray, boxes: np.ndarray, chunk: int = 2048):
+# Ray-box work above which the nearest-hit search is split over host processes (the
+# rays are independent, so the result is the same bits as one process gives).
+_POOL_WORK = 50_000_000
+
+
+def _nearest_hit_part(args):
+    return _nearest_hit_serial(*args)
+
+
+def _nearest_hit(org: np.ndarray, d: np.ndarray, boxes: np.ndarray, chunk: int = 2048, procs: int | None = None):
     """Nearest surface hit of rays (org, d) in the room (float64).
 
     Returns (t, face) where face in [0,5) is a wall, 5 + 6*b + f is face f
     (-x,+x,-y,+y,-z,+z) of box b, and -1 means the ray left through the opening.
+    Large searches run on ``procs`` spawned processes (default: the host cores, at
+    most 16), each on a contiguous share of the rays.
     """
+    nr = org.shape[0]
+    if procs is None:
+        procs = min(16, os.cpu_count() or 1) if nr * max(boxes.shape[0], 1) >= _POOL_WORK else 1
+    if procs > 1 and nr >= 2 * chunk:
+        import multiprocessing
+        cuts = np.linspace(0, nr, procs + 1).astype(np.int64)
+        parts = [(org[a:b], d[a:b], boxes, chunk) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+        with multiprocessing.get_context("spawn").Pool(len(parts)) as pool:
+            res = pool.map(_nearest_hit_part, parts)
+        return np.concatenate([r[0] for r in res]), np.concatenate([r[1] for r in res])
+    return _nearest_hit_serial(org, d, boxes, chunk)
+
+
+def _nearest_hit_serial(org: np.ndarray, d: np.ndarray, boxes: np.ndarray, chunk: int = 2048):
     nr = org.shape[0]
     t_out = np.full(nr, np.inf)
     face_out = np.full(nr, -1, dtype=np.int64)

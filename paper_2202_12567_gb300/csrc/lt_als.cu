@@ -1054,32 +1054,53 @@ __global__ void __launch_bounds__(128) k_als_retry(AlsQueue<RP> q, Omega om, boo
     }
 }
 
-__global__ void k_render(lt_frame F, lt_samples smp, const float* __restrict__ U, const float* __restrict__ V,
-                         int r, const float* __restrict__ w, const int32_t* __restrict__ perm,
-                         float* __restrict__ img) {
+// Image of slice s (Sec. 3): t_s = V_s^T w, then img[perm[i]] = max(0, u_i . t_s).
+// blockIdx.y is the slice; each CTA forms t_s itself (the slice's V rows are read once
+// from DRAM and then from L2): thread x owns component x % r of the columns
+// x / r + c (blockDim / r), c = 0, 1, ... (consecutive threads read consecutive floats),
+// and the partial sums are added in a fixed order.  The CTAs of a slice then split
+// its rows, a thread per row (16-byte loads of u_i when r is a multiple of 4 and U
+// 16-byte aligned).
+__global__ void __launch_bounds__(512) k_render(lt_frame F, lt_samples smp, const float* __restrict__ U,
+                                                const float* __restrict__ V, int r, const float* __restrict__ w,
+                                                const int32_t* __restrict__ perm, float* __restrict__ img) {
+    __shared__ float part[512];
     __shared__ float t[32];
-    __shared__ float part[8][32];
     const int s = blockIdx.y;
     const int ns = smp.ncol[s];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // t_s = V_s^T w: warp wid sums columns wid, wid+8, ...; lane k owns component k
+    const int cpp = (int)blockDim.x / r;  // columns per pass
+    const int col = (int)threadIdx.x / r, k = (int)threadIdx.x - col * r;
     float acc = 0.f;
-    if (lane < r)
-        for (int j = wid; j < ns; j += blockDim.x >> 5)
-            acc += V[((int64_t)s * F.C + j) * r + lane] * (w ? w[(int64_t)s * F.C + j] : 1.f);
-    part[wid][lane] = acc;
+    if (col < cpp) {
+        const float* Vs = V + (int64_t)s * F.C * r;
+        const float* ws = w ? w + (int64_t)s * F.C : nullptr;
+        for (int j = col; j < ns; j += cpp) acc = fmaf(Vs[(int64_t)j * r + k], ws ? ws[j] : 1.f, acc);
+    }
+    part[threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.x < 32) {
+    if ((int)threadIdx.x < r) {
         float a = 0.f;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += part[i][threadIdx.x];
+        for (int c = 0; c < cpp; ++c) a += part[c * r + threadIdx.x];
         t[threadIdx.x] = a;
     }
     __syncthreads();
     const int row0 = F.slice_off[s], ms = F.slice_off[s + 1] - row0;
+    const bool vec = (r & 3) == 0 && ((uintptr_t)U & 15) == 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ms; i += gridDim.x * blockDim.x) {
         const float* u = U + (int64_t)(row0 + i) * r;
         float v = 0.f;
-        for (int k = 0; k < r; ++k) v += u[k] * t[k];
+        if (vec) {
+            const float4* u4 = reinterpret_cast<const float4*>(u);
+            for (int q = 0; q < (r >> 2); ++q) {
+                const float4 x = __ldg(u4 + q);
+                v = fmaf(x.x, t[4 * q], v);
+                v = fmaf(x.y, t[4 * q + 1], v);
+                v = fmaf(x.z, t[4 * q + 2], v);
+                v = fmaf(x.w, t[4 * q + 3], v);
+            }
+        } else {
+            for (int q = 0; q < r; ++q) v = fmaf(__ldg(u + q), t[q], v);
+        }
         img[perm[row0 + i]] = fmaxf(v, 0.f);
     }
 }
@@ -1353,8 +1374,8 @@ extern "C" lt_status lt_render(lt_ctx* ctx, const lt_frame* f, const lt_samples*
         !row_perm || !img)
         return lt_fail(ctx, LT_EINVAL, "lt_render: bad arguments");
     cudaSetDevice(ctx->device);
-    const int per = std::max(1, std::min(64, (int)((f->max_rows + 255) / 256)));
-    k_render<<<dim3(per, f->S), 256, 0, ctx->stream>>>(*f, *smp, uv->U, uv->V, uv->r, w, row_perm, img);
+    const int per = std::max(1, std::min(64, (int)((f->max_rows + 511) / 512)));
+    k_render<<<dim3(per, f->S), 512, 0, ctx->stream>>>(*f, *smp, uv->U, uv->V, uv->r, w, row_perm, img);
     LT_LAUNCH_CHECK(ctx, "k_render");
     return LT_OK;
 }

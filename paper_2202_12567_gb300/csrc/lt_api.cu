@@ -128,7 +128,8 @@ extern "C" lt_status lt_get_tuning(const lt_ctx* ctx, lt_tuning* t) {
 extern "C" lt_status lt_set_tuning(lt_ctx* ctx, const lt_tuning* t) {
     if (!ctx || !t) return LT_EINVAL;
     if (t->eval_ctas_per_sm < 1 || t->eval_ctas_per_sm > 64 || t->ray_ctas_per_sm < 1 || t->ray_ctas_per_sm > 64 ||
-        t->als_lane_entries < 16 || t->als_lane_entries > 1024 || t->als_form < 0 || t->als_form > 1)
+        t->als_lane_entries < 16 || t->als_lane_entries > 1024 || t->als_form < 0 || t->als_form > 1 ||
+        t->p1_form < 0 || t->p1_form > 1)
         return lt_fail(ctx, LT_EINVAL, "lt_set_tuning: value out of range");
     ctx->tune = *t;
     return LT_OK;

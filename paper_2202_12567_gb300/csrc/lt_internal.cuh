@@ -478,7 +478,8 @@ struct lt_ctx {
     const uint64_t* seed_dev = nullptr;    // device seed word of the graph being captured
     std::vector<void*> retired;            // scratch that live graphs may still reference
     int graphs = 0;                        // graphs alive on this context
-    lt_tuning tune{16, 16, 96, 0};            // launch tuning (lt_set_tuning)
+    lt_tuning tune{16, 16, 96, 0, 0};         // launch tuning (lt_set_tuning)
+    int p1_walk_blocks = 0;                // resident blocks per SM of the persistent pass-1 walk
     int64_t scratch_limit = 0;             // bytes of scratch the context may hold (0: no limit)
 };
 

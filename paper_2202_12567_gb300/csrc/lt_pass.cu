@@ -102,12 +102,14 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_plan(lt_frame F, float rat
 }
 
 // ------------------------------------------------------------------ pass 1: flat kernels
-// Every kernel below runs over all slices at once.  Per forest level: k_p1_setup
-// lays out the union of each testable sibling pair and queues the entries it lacks,
-// k_p1_rays evaluates the queue (one shadow ray per thread), k_p1_decide reduces
-// eps, applies Eq. 2 and merges or rejects.  Pairs with more than kThreadPair rows
-// are laid out and decided by a warp each.
-constexpr int kThreadPair = 64;
+// Every step below runs over all slices at once.  Per forest level: setup lays out
+// the union of each testable sibling pair and queues the entries it lacks (small
+// pairs by a thread, big ones by a CTA), rays evaluates the queue (one shadow ray
+// per thread), decide reduces eps, applies Eq. 2 and merges or rejects.  The levels
+// run either as separate launches per step (the default: on the 256x256, 16K-VPL
+// frame 2.07 ms) or inside one persistent cooperative launch with grid-wide
+// barriers between the steps (k_p1_walk, 2.52 ms there: the steps are chains of
+// dependent loads, and a grid barrier costs more than a launch inside a graph).
 
 struct P1Store {
     int32_t* rows;     // [total] row of each storage slot
@@ -127,6 +129,7 @@ struct P1Work {
     int32_t* mpt;      // [mcap] slice-ordered point of the entry
     int32_t* mnode;    // [mcap] tree node of the entry's column
     int64_t* big;      // [bcap] flat pair index of a big pair
+    unsigned* bar;     // arrival counter of the persistent walk's grid barriers
     int64_t mcap, bcap;
 };
 
@@ -415,71 +418,81 @@ __device__ __forceinline__ void put_missing(const P1Work& w, long long q, int64_
     }
 }
 
-// -- level h, step 1: union layout of every testable pair, queue of missing entries
-__global__ void k_p1_setup(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h, int32_t* status) {
+// -- level h, step 1: union layout of every testable pair, queue of missing entries.
+// A pair of at most kThreadPair rows is laid out by one thread (a serial merge of
+// the two sorted lists, once to count the rows that only one list holds and once to
+// write), a bigger one by a CTA (queued as big).
+constexpr int kThreadPair = 64;
+
+__device__ __forceinline__ bool pair_big(const PairCtx& pc) { return pc.na + pc.nb > kThreadPair; }
+
+__device__ __forceinline__ int serial_missing(const PairCtx& pc) {
+    int i = 0, j = 0, nmiss = 0;
+    while (i < pc.na || j < pc.nb) {
+        const int xa = i < pc.na ? pc.ra[i] : 0x7fffffff, xb = j < pc.nb ? pc.rb[j] : 0x7fffffff;
+        if (xa < xb) ++i, ++nmiss;
+        else if (xb < xa) ++j, ++nmiss;
+        else ++i, ++j;
+    }
+    return nmiss;
+}
+
+__device__ __forceinline__ void serial_write(const lt_frame& F, const P1Plan& pl, const P1Store& st, const P1Work& w,
+                                             const PairCtx& pc, long long q, int32_t* status) {
+    const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b];
+    int32_t* rf = st.rows + pc.iff;
+    float* fa = st.v0 + pc.iff;
+    float* fb = st.v1 + pc.iff;
+    int i = 0, j = 0, n = 0;
+    while (i < pc.na || j < pc.nb) {
+        const int xa = i < pc.na ? pc.ra[i] : 0x7fffffff, xb = j < pc.nb ? pc.rb[j] : 0x7fffffff;
+        if (xa < xb) {
+            rf[n] = xa;
+            fa[n] = st.v0[pc.ia + i++];
+            put_missing(w, q++, st.total + pc.iff + n, pc.row0 + xa, tb, status);   // V_b(xa)
+        } else if (xb < xa) {
+            rf[n] = xb;
+            fb[n] = st.v0[pc.ib + j++];
+            put_missing(w, q++, pc.iff + n, pc.row0 + xb, ta, status);              // V_a(xb)
+        } else {
+            rf[n] = xa;
+            fa[n] = st.v0[pc.ia + i++];
+            fb[n] = st.v0[pc.ib + j++];
+        }
+        ++n;
+    }
+    pl.cnt[(int64_t)pc.s * (2 * F.C - 1) + pc.f] = n;
+}
+
+__device__ __forceinline__ void p1_setup_body(const lt_frame& F, const P1Plan& pl, const P1Store& st, const P1Work& w,
+                                              int h, int32_t* status) {
     const int np = F.level_off[h + 1] - F.level_off[h];
-    const int NF = 2 * F.C - 1;
     const int64_t npairs = (int64_t)F.S * np;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // warp-uniform trip count so that every lane takes part in the reservations
     for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < npairs; t0 += stride) {
         const int64_t t = t0 + threadIdx.x;
         PairCtx pc;
-        bool active = t < npairs && load_pair(F, pl, st, h, t, pc);
-        const bool big = active && pc.na + pc.nb > kThreadPair;
+        const bool active = t < npairs && load_pair(F, pl, st, h, t, pc);
+        const bool big = active && pair_big(pc);
         const long long qb = warp_reserve((unsigned long long*)&w.bcount[h], big ? 1 : 0);
         if (big) {
             if (qb < w.bcap) w.big[qb] = t;
             else latch(status, LT_ELIMIT);
-            active = false;
         }
-        // count the missing entries (rows in only one of the two sets)
-        int nmiss = 0;
-        if (active) {
-            int i = 0, j = 0;
-            while (i < pc.na || j < pc.nb) {
-                const int xa = i < pc.na ? pc.ra[i] : 0x7fffffff, xb = j < pc.nb ? pc.rb[j] : 0x7fffffff;
-                if (xa < xb) ++i, ++nmiss;
-                else if (xb < xa) ++j, ++nmiss;
-                else ++i, ++j;
-            }
-        }
-        long long q = warp_reserve((unsigned long long*)&w.mcount[h], nmiss);
-        if (!active) continue;
-        const int ta = F.forest[8 * pc.a], tb = F.forest[8 * pc.b];
-        int32_t* rf = st.rows + pc.iff;
-        float* fa = st.v0 + pc.iff;
-        float* fb = st.v1 + pc.iff;
-        int i = 0, j = 0, n = 0;
-        while (i < pc.na || j < pc.nb) {
-            const int xa = i < pc.na ? pc.ra[i] : 0x7fffffff, xb = j < pc.nb ? pc.rb[j] : 0x7fffffff;
-            if (xa < xb) {
-                rf[n] = xa;
-                fa[n] = st.v0[pc.ia + i++];
-                put_missing(w, q++, st.total + pc.iff + n, pc.row0 + xa, tb, status);   // V_b(xa)
-            } else if (xb < xa) {
-                rf[n] = xb;
-                fb[n] = st.v0[pc.ib + j++];
-                put_missing(w, q++, pc.iff + n, pc.row0 + xb, ta, status);              // V_a(xb)
-            } else {
-                rf[n] = xa;
-                fa[n] = st.v0[pc.ia + i++];
-                fb[n] = st.v0[pc.ib + j++];
-            }
-            ++n;
-        }
-        pl.cnt[(int64_t)pc.s * NF + pc.f] = n;
+        const bool mine = active && !big;
+        const long long q = warp_reserve((unsigned long long*)&w.mcount[h], mine ? serial_missing(pc) : 0);
+        if (mine) serial_write(F, pl, st, w, pc, q, status);
     }
 }
 
-// the same for pairs with more than kThreadPair rows, one CTA per pair: both sorted
-// row lists staged in shared memory (global reads beyond kBigStage rows), the union
-// slot of a row = its index + its rank in the other list - the common rows before it
-// (a block scan of the "in both" flags)
+// big pairs, one CTA per pair: both sorted row lists staged in shared memory (global
+// reads beyond kBigStage rows), the slot of a row from its rank in the other list
+// (binary search) and a block scan of the "in both" flags
 constexpr int kBigStage = 4096;
 
-__global__ void __launch_bounds__(256) k_p1_setup_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h,
-                                                      int32_t* status) {
+__device__ __forceinline__ void p1_setup_big_body(const lt_frame& F, const P1Plan& pl, const P1Store& st,
+                                                  const P1Work& w, int h, int32_t* status) {
     __shared__ int32_t sa[kBigStage], sb[kBigStage];
     __shared__ int32_t ws[32];
     const int NF = 2 * F.C - 1;
@@ -548,8 +561,8 @@ __global__ void __launch_bounds__(256) k_p1_setup_big(lt_frame F, P1Plan pl, P1S
 }
 
 // -- level h, step 2: the queued entries, one shadow ray per thread
-__global__ void __launch_bounds__(128) k_p1_rays(lt_frame F, Grid g, float dmin2, P1Store st, P1Work w, int h,
-                                                 int32_t* status) {
+__device__ __forceinline__ void p1_rays_body(const lt_frame& F, const Grid& g, float dmin2, const P1Store& st,
+                                             const P1Work& w, int h, int32_t* status) {
     const float4* pts = reinterpret_cast<const float4*>(F.pts);
     const float4* vpls = reinterpret_cast<const float4*>(F.vpls);
     const int64_t n = min(w.mcount[h], w.mcap);
@@ -614,21 +627,24 @@ __device__ __forceinline__ float pair_eps(const lt_frame& F, const P1Store& st, 
     return e;
 }
 
-__global__ void k_p1_decide(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+// pairs that are not big, one thread per pair
+__device__ __forceinline__ void p1_decide_body(const lt_frame& F, const P1Plan& pl, const P1Store& st,
+                                               const P1Work& w, int h) {
     const int np = F.level_off[h + 1] - F.level_off[h];
     const int NF = 2 * F.C - 1;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)F.S * np;
          t += (int64_t)gridDim.x * blockDim.x) {
         PairCtx pc;
         if (!load_pair(F, pl, st, h, t, pc)) continue;
-        if (pc.na + pc.nb > kThreadPair) continue;
+        if (pair_big(pc)) continue;
         const int nf = pl.cnt[(int64_t)pc.s * NF + pc.f];
         decide_pair(F, pl, st, w.thr, pc, pair_eps(F, st, pc, nf, 0, 1), 0, 1, true);
     }
 }
 
 // big pairs, one CTA per pair
-__global__ void __launch_bounds__(256) k_p1_decide_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+__device__ __forceinline__ void p1_decide_big_body(const lt_frame& F, const P1Plan& pl, const P1Store& st,
+                                                   const P1Work& w, int h) {
     __shared__ float red[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int NF = 2 * F.C - 1;
@@ -644,6 +660,80 @@ __global__ void __launch_bounds__(256) k_p1_decide_big(lt_frame F, P1Plan pl, P1
         float em = 0.f;
         for (int k = 0; k < nw; ++k) em = fmaxf(em, red[k]);
         decide_pair(F, pl, st, w.thr, pc, em, threadIdx.x, blockDim.x, threadIdx.x == 0);
+    }
+}
+
+// Per-level form: each step of each level is its own launch.
+__global__ void __launch_bounds__(128) k_p1_setup(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h,
+                                                  int32_t* status) {
+    p1_setup_body(F, pl, st, w, h, status);
+}
+__global__ void __launch_bounds__(256) k_p1_setup_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h,
+                                                      int32_t* status) {
+    p1_setup_big_body(F, pl, st, w, h, status);
+}
+__global__ void __launch_bounds__(128) k_p1_rays(lt_frame F, Grid g, float dmin2, P1Store st, P1Work w, int h,
+                                                 int32_t* status) {
+    p1_rays_body(F, g, dmin2, st, w, h, status);
+}
+__global__ void __launch_bounds__(128) k_p1_decide(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+    p1_decide_body(F, pl, st, w, h);
+}
+__global__ void __launch_bounds__(256) k_p1_decide_big(lt_frame F, P1Plan pl, P1Store st, P1Work w, int h) {
+    p1_decide_big_body(F, pl, st, w, h);
+}
+
+// Persistent form: one cooperative launch walks every level, the four steps of a level
+// separated by grid-wide barriers.  `bar` counts block arrivals (zeroed before the
+// launch); barrier k is passed when it reaches k * gridDim.x.  Every wait is bounded:
+// past the limit the block latches LT_ELIMIT and leaves the walk (so do the others at
+// their next barrier, also bounded).
+constexpr unsigned kBarSpins = 1u << 21;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& k, int32_t* status, int* s_ok) {
+    __syncthreads();
+    ++k;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned target = k * gridDim.x;
+        int ok = 1;
+        for (unsigned it = 0; ld_acquire_gpu(bar) < target; ++it) {
+            if (it >= kBarSpins) {
+                ok = 0;
+                latch(status, LT_ELIMIT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(256, 3) k_p1_walk(lt_frame F, Grid g, float dmin2, P1Plan pl, P1Store st, P1Work w,
+                                                 int32_t* status) {
+    __shared__ int s_ok;
+    unsigned k = 0;
+    for (int h = 1; h <= F.H; ++h) {
+        if (F.level_off[h + 1] == F.level_off[h]) continue;  // uniform over the grid
+        p1_setup_body(F, pl, st, w, h, status);
+        if (!grid_barrier(w.bar, k, status, &s_ok)) return;
+        p1_setup_big_body(F, pl, st, w, h, status);
+        if (!grid_barrier(w.bar, k, status, &s_ok)) return;
+        p1_rays_body(F, g, dmin2, st, w, h, status);
+        if (!grid_barrier(w.bar, k, status, &s_ok)) return;
+        p1_decide_body(F, pl, st, w, h);
+        p1_decide_big_body(F, pl, st, w, h);
+        if (!grid_barrier(w.bar, k, status, &s_ok)) return;
     }
 }
 
@@ -1149,18 +1239,19 @@ lt_status sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, i
     w.kpfx = (int64_t*)wtake((size_t)(S + 1) * 8);
     w.leafmean = (float*)wtake((size_t)S * C * 4);
     w.thr = (float*)wtake((size_t)S * 4);
-    w.mcount = (int64_t*)wtake((size_t)Hn * 8);
+    w.mcount = (int64_t*)wtake((size_t)Hn * 8 + 8);
     w.bcount = (int64_t*)wtake((size_t)Hn * 8);
     w.mdst = (int64_t*)wtake((size_t)mcap * 8);
     w.mpt = (int32_t*)wtake((size_t)mcap * 4);
     w.mnode = (int32_t*)wtake((size_t)mcap * 4);
     w.big = (int64_t*)wtake((size_t)bcap * 8);
+    w.bar = (unsigned*)(w.mcount + Hn);  // shares the zeroing of the level counters
     w.mcap = mcap;
     w.bcap = bcap;
     float* effs = target > 0 ? (float*)wtake(eff_bytes) : nullptr;
     if ((size_t)(wp - q) > ctx->scr_size[SCR_P1_STORE])
         return lt_fail(ctx, LT_ENOMEM, "lt_sample_pass1: work layout overflow");
-    LT_CUDA(ctx, cudaMemsetAsync(w.mcount, 0, (size_t)Hn * 8, ctx->stream));
+    LT_CUDA(ctx, cudaMemsetAsync(w.mcount, 0, (size_t)Hn * 8 + 8, ctx->stream));
     LT_CUDA(ctx, cudaMemsetAsync(w.bcount, 0, (size_t)Hn * 8, ctx->stream));
     const int nsm = ctx->num_sms;
     const float dmin2 = d_min * d_min;
@@ -1196,7 +1287,28 @@ lt_status sample_pass1(lt_ctx* ctx, const lt_frame* f, float rate1, float tau, i
         LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         ctx->plan.level_off = loff;
     }
-    for (int h = 1; h <= f->H; ++h) {
+    const bool walk = ctx->tune.p1_form == 1 && f->H > 0;
+    if (walk) {
+        if (ctx->p1_walk_blocks == 0) {
+            int nb = 0;
+            LT_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_p1_walk, 256, 0));
+            ctx->p1_walk_blocks = std::max(1, std::min(nb, 8));
+        }
+        // every block resident at once (the cooperative launch checks it)
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(ctx->p1_walk_blocks * nsm));
+        lc.blockDim = dim3(256);
+        lc.dynamicSmemBytes = 0;
+        lc.stream = ctx->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        LT_CUDA(ctx, cudaLaunchKernelEx(&lc, k_p1_walk, *f, ctx->grid, dmin2, pl, store, w, ctx->d_status));
+        LT_LAUNCH_CHECK(ctx, "k_p1_walk");
+    }
+    for (int h = 1; h <= f->H && !walk; ++h) {
         const int64_t npairs = (int64_t)S * (loff[h + 1] - loff[h]);
         if (npairs == 0) continue;
         k_p1_setup<<<grid_for(npairs, 128), 128, 0, ctx->stream>>>(*f, pl, store, w, h, ctx->d_status);

@@ -74,7 +74,7 @@ MLP_FEATURES, MLP_HIDDEN, MLP_PARAMS = 32, 64, 10497
 
 class lt_tuning(ctypes.Structure):
     _fields_ = [("eval_ctas_per_sm", _i32), ("ray_ctas_per_sm", _i32), ("als_lane_entries", _i32),
-                ("als_form", _i32)]
+                ("als_form", _i32), ("p1_form", _i32)]
 
 
 _SIGS = {

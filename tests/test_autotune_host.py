@@ -21,7 +21,7 @@ def test_candidates_are_valid_tuning_values():
         assert cands == sorted(set(cands))
         if name.endswith("ctas_per_sm"):
             assert all(1 <= c <= 64 for c in cands)
-        elif name == "als_form":
+        elif name in ("als_form", "p1_form"):
             assert cands == [0, 1]
         else:
             assert all(16 <= c <= 1024 for c in cands)

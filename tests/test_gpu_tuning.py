@@ -23,7 +23,7 @@ def R():
 def test_tuning_round_trip_and_validation(R):
     from paper_2202_12567_gb300 import lt
     t0 = lt.lt_get_tuning(R.ctx)
-    assert t0 == dict(eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0)
+    assert t0 == dict(eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0, p1_form=0)
     lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=4)
     assert lt.lt_get_tuning(R.ctx)["eval_ctas_per_sm"] == 4
     with pytest.raises(lt.LtError):
@@ -32,6 +32,8 @@ def test_tuning_round_trip_and_validation(R):
     with pytest.raises(lt.LtError):
         lt.lt_set_tuning(R.ctx, als_form=2)
     assert lt.lt_get_tuning(R.ctx)["als_form"] == 0
+    with pytest.raises(lt.LtError):
+        lt.lt_set_tuning(R.ctx, p1_form=-1)
     lt.lt_set_tuning(R.ctx, **t0)
 
 
@@ -40,6 +42,13 @@ def test_launch_shapes_do_not_change_results(R):
     base = R.render_frame(seed=5).clone()
     lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=3, ray_ctas_per_sm=33)
     assert torch.equal(R.render_frame(seed=5), base)
+    lt.lt_set_tuning(R.ctx, p1_form=1)  # pass-1 levels in one persistent launch: the same bits
+    assert torch.equal(R.render_frame(seed=5), base)
+    R.capture()  # the cooperative launch inside a captured frame graph
+    assert torch.equal(R.render_graph(seed=5), base)
+    R.graph.close()
+    R.graph = None
+    lt.lt_set_tuning(R.ctx, p1_form=0)
     lt.lt_set_tuning(R.ctx, als_lane_entries=16)  # other lane groups: only the sum order changes
     img = R.render_frame(seed=5)
     rel = float(torch.linalg.norm(img.double() - base.double()) / torch.linalg.norm(base.double()))
@@ -48,7 +57,7 @@ def test_launch_shapes_do_not_change_results(R):
     img = R.render_frame(seed=5)
     rel = float(torch.linalg.norm(img.double() - base.double()) / torch.linalg.norm(base.double()))
     assert rel < 1e-3  # the completion tolerance: another summation order over 10 sweeps
-    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0)
+    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0, p1_form=0)
 
 
 def test_autotuner_picks_candidates_and_caches(R, tmp_path):
@@ -59,7 +68,7 @@ def test_autotuner_picks_candidates_and_caches(R, tmp_path):
     for name, (cands, _) in autotune.CANDIDATES.items():
         assert values[name] in cands
     assert lt.lt_get_tuning(R.ctx) == values
-    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0)
+    lt.lt_set_tuning(R.ctx, eval_ctas_per_sm=16, ray_ctas_per_sm=16, als_lane_entries=96, als_form=0, p1_form=0)
     key2, values2, cached2 = autotune.apply(R, "room64_vpl1k_2box", path=path)
     assert cached2 and key2 == key and values2 == values and lt.lt_get_tuning(R.ctx) == values
     assert key in json.load(open(path))
