@@ -387,126 +387,66 @@ __global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int R, const in
     }
 }
 
-// ---- Gram matrices on the tensor cores ---------------------------------------
-// For one line (a row of U or of V) with observed entries e and gathered factor rows
-// x_e (r values each), G = sum_e x_e x_e^T = X^T X and b = sum_e a_e x_e.  X^T X is a
-// 16 x K x 16 contraction per line: mma.m16n8k8 with A = X^T (16 x 8) and B = X
-// (8 x 8) whose fragments hold the same gathered values.  Each float is split into
-// a TF32 head and a TF32 tail (x = hi + lo) and the three products hi*hi, hi*lo,
-// lo*hi are accumulated in FP32, which keeps the Gram at float32 accuracy.
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
-    hi = to_tf32(x);
-    lo = to_tf32(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float& c0, float& c1, float& c2, float& c3, uint32_t a0, uint32_t a1,
-                                         uint32_t a2, uint32_t a3, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// Whole warp: Gram and right-hand side of one line into shared memory
-// Gs[RP][RP+1] and bs[RP] (RP = 16 or 32, rows and columns >= r are zero).
-template <int RP>
-__device__ __forceinline__ void gram_tc(int len, const uint16_t* __restrict__ idx, const float* __restrict__ val,
-                                        const float* Fb, int fstride, int r, float* Gs, float* bs) {
-    constexpr int MT = RP / 16, NT = RP / 8;
+// ---- Gram of one line by one warp (ranks above 16) ---------------------------
+// For one line (a row of U or of V) with observed entries e and factor rows x_e,
+// G = sum_e x_e x_e^T and b = sum_e a_e x_e.  Lane k accumulates row k of G (all RP
+// columns; G is symmetric) and b_k: for each entry the warp reads x_e with 16-byte
+// loads at one warp-uniform address (a broadcast from L1/L2) and lane k its own
+// component x_e[k], then adds x_e[k] x_e and a_e x_e[k].  The rows have stride R;
+// components at or beyond R are zero.  Rows k of G go to Gs[RP][RP+1], b to bs[RP].
+template <int RP>  // RP == 32: lane k holds row k
+__device__ __forceinline__ void gram_warp(int len, const uint16_t* __restrict__ idx, const float* __restrict__ val,
+                                          const float* __restrict__ src, int R, float* Gs, float* bs) {
+    static_assert(RP == 32, "one lane per Gram row");
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    float c[MT][NT][4];
+    const int lane = threadIdx.x & 31;
+    const bool vec = (R & 3) == 0 && ((uintptr_t)src & 15) == 0;
+    float g[RP];
 #pragma unroll
-    for (int i = 0; i < MT; ++i)
-#pragma unroll
-        for (int j = 0; j < NT; ++j)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) c[i][j][q] = 0.f;
-    float bpart[MT][2];
-#pragma unroll
-    for (int i = 0; i < MT; ++i) bpart[i][0] = bpart[i][1] = 0.f;
+    for (int c = 0; c < RP; ++c) g[c] = 0.f;
+    float b = 0.f;
     for (int e0 = 0; e0 < len; e0 += 32) {
-        const int je = e0 + lane < len ? (int)idx[e0 + lane] : -1;
-        const float ae = e0 + lane < len ? val[e0 + lane] : 0.f;
+        const int n = min(32, len - e0);
+        const int je = lane < n ? (int)idx[e0 + lane] : 0;
+        const float ae = lane < n ? val[e0 + lane] : 0.f;
+#pragma unroll 2
+        for (int q = 0; q < n; ++q) {  // n is warp-uniform
+            const int j = __shfl_sync(FULL, je, q);
+            const float a = __shfl_sync(FULL, ae, q);
+            const float* xr = src + (int64_t)j * R;
+            float x[RP];
+            if (vec) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (e0 + 8 * q >= len) break;  // uniform in the warp
-            const int j0 = __shfl_sync(FULL, je, 8 * q + t), j1 = __shfl_sync(FULL, je, 8 * q + t + 4);
-            const float a0v = __shfl_sync(FULL, ae, 8 * q + t), a1v = __shfl_sync(FULL, ae, 8 * q + t + 4);
-            // x[mt][0] = X[t][16mt+g], [1] = X[t][16mt+g+8], [2] = X[t+4][16mt+g], [3] = X[t+4][16mt+g+8]
-            float x[MT][4];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const int m0 = 16 * mt + g, m1 = m0 + 8;
-                x[mt][0] = (j0 >= 0 && m0 < r) ? Fb[j0 * fstride + m0] : 0.f;
-                x[mt][1] = (j0 >= 0 && m1 < r) ? Fb[j0 * fstride + m1] : 0.f;
-                x[mt][2] = (j1 >= 0 && m0 < r) ? Fb[j1 * fstride + m0] : 0.f;
-                x[mt][3] = (j1 >= 0 && m1 < r) ? Fb[j1 * fstride + m1] : 0.f;
-                bpart[mt][0] += a0v * x[mt][0] + a1v * x[mt][2];
-                bpart[mt][1] += a0v * x[mt][1] + a1v * x[mt][3];
-            }
-            uint32_t hi[MT][4], lo[MT][4];
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int i = 0; i < 4; ++i) split_tf32(x[mt][i], hi[mt][i], lo[mt][i]);
-            // B of column tile nt (columns 8nt .. 8nt+7): (X[t][8nt+g], X[t+4][8nt+g])
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    const int bm = nt >> 1, bo = nt & 1;  // rows 8nt+g live in x[bm][bo], x[bm][bo+2]
-                    float* cc = c[mt][nt];
-                    mma_tf32(cc[0], cc[1], cc[2], cc[3], hi[mt][0], hi[mt][1], hi[mt][2], hi[mt][3], hi[bm][bo],
-                             hi[bm][bo + 2]);
-                    mma_tf32(cc[0], cc[1], cc[2], cc[3], hi[mt][0], hi[mt][1], hi[mt][2], hi[mt][3], lo[bm][bo],
-                             lo[bm][bo + 2]);
-                    mma_tf32(cc[0], cc[1], cc[2], cc[3], lo[mt][0], lo[mt][1], lo[mt][2], lo[mt][3], hi[bm][bo],
-                             hi[bm][bo + 2]);
+                for (int c4 = 0; c4 < RP / 4; ++c4) {
+                    const float4 t = 4 * c4 < R ? __ldg(reinterpret_cast<const float4*>(xr) + c4)
+                                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[4 * c4] = t.x;
+                    x[4 * c4 + 1] = t.y;
+                    x[4 * c4 + 2] = t.z;
+                    x[4 * c4 + 3] = t.w;
                 }
+            } else {
+#pragma unroll
+                for (int c = 0; c < RP; ++c) x[c] = c < R ? __ldg(xr + c) : 0.f;
+            }
+            const float xk = lane < R ? __ldg(xr + lane) : 0.f;
+            b = fmaf(a, xk, b);
+#pragma unroll
+            for (int c = 0; c < RP; ++c) g[c] = fmaf(xk, x[c], g[c]);
         }
     }
-    // C fragment: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1) of each 16 x 8 tile
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-            const int row = 16 * mt + g, col = 8 * nt + 2 * t;
-            Gs[row * (RP + 1) + col] = c[mt][nt][0];
-            Gs[row * (RP + 1) + col + 1] = c[mt][nt][1];
-            Gs[(row + 8) * (RP + 1) + col] = c[mt][nt][2];
-            Gs[(row + 8) * (RP + 1) + col + 1] = c[mt][nt][3];
-        }
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float v = bpart[mt][h];
-            v += __shfl_xor_sync(FULL, v, 1);
-            v += __shfl_xor_sync(FULL, v, 2);
-            if (t == 0) bs[16 * mt + 8 * h + g] = v;
-        }
+    for (int c = 0; c < RP; ++c) Gs[lane * (RP + 1) + c] = g[c];
+    bs[lane] = b;
 }
 
-// A group of G lanes solves (Gram + ridge) u = b for one line: lane k loads row k of
-// the Gram Gs (row stride G + 1) and b_k into registers.  Returns false when the
-// float factorisation is not acceptable (a non-positive pivot, or pivots spread by
-// more than 1/kPivotRatio).
+// A group of G lanes solves (Gram + ridge) u = b for one line: lane k holds row k of
+// the Gram in acc and b_k in rhs.  Returns false when the float factorisation is not
+// acceptable (a non-positive pivot, or pivots spread by more than 1/kPivotRatio).
 template <int G, typename T, bool SMEM_L>
-__device__ __forceinline__ bool factor_solve(const float* Gs, const float* bs, bool live, int len, int r,
-                                             float lam_rel, int k, T* out_k, bool check, float* Lsh) {
+__device__ __forceinline__ bool factor_solve_rows(T (&acc)[G], T rhs, bool live, int len, int r, float lam_rel,
+                                                  int k, T* out_k, bool check, float* Lsh) {
     const unsigned FULL = 0xffffffffu;
-    T acc[G];
-#pragma unroll
-    for (int c = 0; c < G; ++c) acc[c] = live ? (T)Gs[k * (G + 1) + c] : T(0);
-    T rhs = live ? (T)bs[k] : T(0);
     if (!live) len = 0;
     T tr = T(0);
 #pragma unroll
@@ -603,25 +543,33 @@ __device__ __forceinline__ bool factor_solve(const float* Gs, const float* bs, b
     return true;
 }
 
-// One half-step: rows of U (rows_side) or columns of V, slice by slice.  CTA
-// (p, s) takes the p-th of P equal parts of the lines of slice s.  The other side's
-// factor of the slice (V_s for the U-step, U_s for the V-step) is staged in shared
-// memory with row stride RP + 1 when it fits, so that the gathers of the Gram are
-// shared-memory loads; a warp builds the Grams of its lines on the tensor cores and
-// groups of RP lanes factor and solve them.
+// the same with row k of the Gram and b_k read from Gs [G][G + 1] and bs
+template <int G, typename T, bool SMEM_L>
+__device__ __forceinline__ bool factor_solve(const float* Gs, const float* bs, bool live, int len, int r,
+                                             float lam_rel, int k, T* out_k, bool check, float* Lsh) {
+    T acc[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) acc[c] = live ? (T)Gs[k * (G + 1) + c] : T(0);
+    const T rhs = live ? (T)bs[k] : T(0);
+    return factor_solve_rows<G, T, SMEM_L>(acc, rhs, live, len, r, lam_rel, k, out_k, check, Lsh);
+}
+
+// One half-step for ranks above 16: rows of U (rows_side) or columns of V, slice by
+// slice.  CTA (p, s) takes the p-th of P equal parts of the lines of slice s; a warp
+// builds the Gram of one line at a time (gram_warp, the other side's factor rows
+// read from L2) and factors and solves it in the warp in float32; a line whose
+// pivots fail the check goes to the float64 pass (k_als_retry).
 template <int RP>
 __host__ __device__ constexpr int als_warps() { return RP == 32 ? 8 : 16; }
 
 template <int RP>
-__global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F, lt_samples smp, Omega om, int R,
+__global__ void __launch_bounds__(32 * als_warps<RP>(), 2) k_als_half(lt_frame F, lt_samples smp, Omega om, int R,
                                                                    const int32_t* __restrict__ rk,
                                                                    float lam_rel, bool rows_side,
                                                                    const float* __restrict__ Fin,
-                                                                   float* __restrict__ Fout, int32_t* n_fp64,
-                                                                   int stage_rows) {
+                                                                   float* __restrict__ Fout, AlsQueue<RP> aq) {
     constexpr int LPW = 32 / RP;  // lines per warp
     constexpr int NW = als_warps<RP>();
-    extern __shared__ float stage[];                       // [stage_rows][RP + 1]
     __shared__ float Gs_all[NW][LPW][RP * (RP + 1)];
     __shared__ float bs_all[NW][LPW][RP];
     const int s = blockIdx.y, P = gridDim.x, p = blockIdx.x;
@@ -635,67 +583,64 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 1) k_als_half(lt_frame F
     const int l0 = (int)((int64_t)nlines * p / P), l1 = (int)((int64_t)nlines * (p + 1) / P);
     if (l0 >= l1) return;
     const float* src = rows_side ? Fin + (int64_t)s * F.C * R : Fin + (int64_t)row0 * R;
-    const int nsrc = rows_side ? ns : ms;
-    const bool staged = nsrc <= stage_rows;
-    if (staged) {
-        for (int i = threadIdx.x; i < nsrc * RP; i += blockDim.x) {
-            const int row = i / RP, c = i % RP;
-            stage[row * (RP + 1) + c] = c < r ? __ldg(src + (int64_t)row * R + c) : 0.f;
-        }
-    }
-    __syncthreads();
-    const float* Fb = staged ? stage : src;
-    const int fstride = staged ? RP + 1 : R;
     const int64_t o = smp.off[s];
     for (int base = l0 + wid * LPW; base < l1; base += NW * LPW) {
         int my_len = 0;
-        float* my_dst = nullptr;
+        int64_t my_dst = 0, my_pos = 0;
 #pragma unroll
         for (int q = 0; q < LPW; ++q) {
             const int line = base + q;
             if (line >= l1) break;  // warp-uniform
-            int len;
+            int len, b;
             const uint16_t* idx;
             const float* vv;
-            float* dst;
+            int64_t dst;
             if (rows_side) {
                 const int32_t* rp = om.rp + row0 + s;
-                const int b = rp[line];
+                b = rp[line];
                 len = rp[line + 1] - b;
                 idx = om.cidx + o + b;
                 vv = om.cval + o + b;
-                dst = Fout + (int64_t)(row0 + line) * R;           // U row
+                dst = (int64_t)(row0 + line) * R;           // U row
             } else {
                 const int32_t* cp = om.cp + (int64_t)s * (F.C + 1);
-                const int b = cp[line];
+                b = cp[line];
                 len = cp[line + 1] - b;
                 idx = om.ridx + o + b;
                 vv = om.rval + o + b;
-                dst = Fout + ((int64_t)s * F.C + line) * R;        // V row
+                dst = ((int64_t)s * F.C + line) * R;        // V row
             }
-            gram_tc<RP>(len, idx, vv, Fb, fstride, r, &Gs_all[wid][q][0], &bs_all[wid][q][0]);
+            gram_warp<RP>(len, idx, vv, src, R, &Gs_all[wid][q][0], &bs_all[wid][q][0]);
             if (grp == q) {
                 my_len = len;
                 my_dst = dst;
+                my_pos = o + b;
             }
         }
         __syncwarp();
         const bool live = base + grp < l1;
         const float* Gs = &Gs_all[wid][grp][0];
         const float* bs = &bs_all[wid][grp][0];
-        float xf;
+        float xf = 0.f;
         const bool okf = factor_solve<RP, float, true>(Gs, bs, live, my_len, r, lam_rel, k, &xf, true,
                                                  &Gs_all[wid][grp][0]);
-        const unsigned bad = __ballot_sync(0xffffffffu, live && !okf);
-        if (bad) {  // float64 retry of the lines whose float pivots were not acceptable
-            double xd;
-            factor_solve<RP, double, false>(Gs, bs, live, my_len, r, lam_rel, k, &xd, false, nullptr);
-            if (live && !okf) {
-                xf = (float)xd;
-                if (k == 0) atomicAdd(n_fp64, 1);
+        if (live && k < R) Fout[my_dst + k] = (okf && k < r) ? xf : 0.f;
+        if (live && !okf && k == 0) {
+            // rare: the float pivots were not acceptable; the line goes to the float64
+            // pass (k_als_retry), which forms its Gram again in float64 from the factor
+            // rows (a Gram summed in float32 would carry its rounding into the solve)
+            const int qs = atomicAdd(aq.count, 1);
+            if (qs < aq.cap) {
+                aq.dst[qs] = my_dst;
+                aq.slot[qs] = my_pos;
+                aq.src[qs] = src - Fin;
+                aq.len[qs] = my_len;
+                aq.grp[qs] = 0;  // contiguous in CSR / CSC
+                aq.rank[qs] = r;
+            } else {
+                latch(aq.status, LT_ELIMIT);
             }
         }
-        if (live && k < R) my_dst[k] = k < r ? xf : 0.f;
         __syncwarp();
     }
 }
@@ -1040,7 +985,19 @@ __global__ void __launch_bounds__(128) k_als_retry(AlsQueue<RP> q, Omega om, boo
         for (int p = 0; p < PER; ++p)
             if (lane + 32 * p < NV) gs[w][lane + 32 * p] = acc[p];
         __syncwarp();
-        if (lane == 0) {
+        if constexpr (RP == 32) {
+            // rank above 16: the warp factors and solves (lane k holds row k), the
+            // Cholesky of one lane would not fit its registers
+            double row[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                row[c] = c <= lane ? gs[w][lane * (lane + 1) / 2 + c] : gs[w][c * (c + 1) / 2 + lane];
+            double xd = 0.0;
+            factor_solve_rows<32, double, false>(row, gs[w][NA + lane], true, len, r, lam_rel, lane, &xd, false,
+                                                 nullptr);
+            if (lane < r) Fout[q.dst[t] + lane] = (float)xd;
+            if (lane == 0) atomicAdd(n_fp64, 1);
+        } else if (lane == 0) {
             double a[NA], b[RP];
             for (int i = 0; i < NA; ++i) a[i] = gs[w][i];
             for (int i = 0; i < RP; ++i) b[i] = gs[w][NA + i];
@@ -1234,13 +1191,16 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     lt_status st = omega_build(ctx, f, smp, E, low && !tc, R > 16 || tc, &om);
     if (st != LT_OK) return st;
     const int RP = R <= 8 ? 8 : 16;  // the low-rank kernels cover ranks up to RP
-    // per half-step retry counters and the float64 count
+    // per half-step retry counters (one set for ranks <= 16, one above) and the
+    // float64 count
+    const bool high = R > 16;
     const int nq = std::max(1, 2 * iters);
-    char* sp = (char*)lt_scratch(ctx, SCR_ALS, (size_t)(nq + 64) * 4 + 256, &st);
+    char* sp = (char*)lt_scratch(ctx, SCR_ALS, (size_t)(2 * nq + 64) * 4 + 256, &st);
     if (!sp) return st;
     int32_t* n64 = (int32_t*)sp;
     int32_t* qcount = n64 + 64;
-    LT_CUDA(ctx, cudaMemsetAsync(n64, 0, (size_t)(nq + 64) * 4, ctx->stream));
+    int32_t* qcount_hi = qcount + nq;
+    LT_CUDA(ctx, cudaMemsetAsync(n64, 0, (size_t)(2 * nq + 64) * 4, ctx->stream));
     const int nsm = ctx->num_sms;
     k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, R, rk, seed_ref(ctx, seed), uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
@@ -1252,10 +1212,16 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const int64_t cap = std::min<int64_t>(std::max<int64_t>(f->m, (int64_t)S * C), 1 << 18);
     int64_t *qdst = nullptr, *qslot = nullptr, *qsrc = nullptr;
     int32_t *qlen = nullptr, *qgrp = nullptr, *qrank = nullptr;
-    if (low) {
+    AlsQueue<32> qhi{};
+    if (low || high) {
         const size_t a8 = ((size_t)cap * 8 + 255) & ~(size_t)255, a4 = ((size_t)cap * 4 + 255) & ~(size_t)255;
-        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, 3 * a8 + 3 * a4, &st);
+        const size_t set = 3 * a8 + 3 * a4;
+        char* qp = (char*)lt_scratch(ctx, SCR_GRAM, 2 * set, &st);
         if (!qp) return st;
+        char* hp = qp + set;  // the queue of the lines above rank 16
+        qhi = AlsQueue<32>{nullptr, (int64_t*)hp, (int64_t*)(hp + a8), (int64_t*)(hp + 2 * a8),
+                           (int32_t*)(hp + 3 * a8), (int32_t*)(hp + 3 * a8 + a4), (int32_t*)(hp + 3 * a8 + 2 * a4),
+                           cap, ctx->d_status};
         qdst = (int64_t*)qp;
         qslot = (int64_t*)(qp + a8);
         qsrc = (int64_t*)(qp + 2 * a8);
@@ -1269,14 +1235,9 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         else
             LT_CUDA(ctx, cudaFuncSetAttribute(k_als_line<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     }
-    // warp-group kernel: ranks above 16 on the tensor cores
-    const int P = std::max(1, (2 * ctx->num_sms + S - 1) / S);
-    const size_t hstat = (size_t)8 * (32 * 33 + 32) * 4;
-    const size_t hbudget = (size_t)210 * 1024 > hstat ? (size_t)210 * 1024 - hstat : 0;
-    const int hstage_rows = (int)std::min<size_t>(hbudget / (33 * 4), (size_t)1 << 20);
-    const size_t hdyn = (size_t)hstage_rows * 33 * 4;
-    if (R > 16)
-        LT_CUDA(ctx, cudaFuncSetAttribute(k_als_half<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hdyn));
+    // warp-per-line kernel for ranks above 16: each slice's lines split over P CTAs
+    // (about 16 CTAs per SM in all, so that uneven slices balance)
+    const int P = std::max(1, (16 * ctx->num_sms + S - 1) / S);
     TcPlan tcp{};
     if (tc) {
         st = als_tc_plan(ctx, f, smp, om, E, R, rk, RP, 2 * iters, &tcp);
@@ -1315,10 +1276,14 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
                 k_als_retry<16><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
                 LT_LAUNCH_CHECK(ctx, "k_als_retry");
             }
-            if (R > 16) {
-                k_als_half<32><<<dim3(P, S), 32 * als_warps<32>(), hdyn, ctx->stream>>>(
-                    *f, *smp, om, R, rk, lam_rel, rows, fin, fout, n64, hstage_rows);
+            if (high) {
+                AlsQueue<32> q = qhi;
+                q.count = qcount_hi + 2 * it + side;
+                k_als_half<32><<<dim3(P, S), 32 * als_warps<32>(), 0, ctx->stream>>>(
+                    *f, *smp, om, R, rk, lam_rel, rows, fin, fout, q);
                 LT_LAUNCH_CHECK(ctx, "k_als_half");
+                k_als_retry<32><<<nsm, 128, 0, ctx->stream>>>(q, om, rows, fin, R, lam_rel, fout, n64);
+                LT_LAUNCH_CHECK(ctx, "k_als_retry");
             }
         }
     }

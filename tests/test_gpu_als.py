@@ -114,12 +114,13 @@ def _thin_row_slices(rng, S, m_s, n_s, r, thin_every, k_thin, k_full):
     return out
 
 
-@pytest.mark.parametrize("form", [1, 0])
-@pytest.mark.parametrize("r", [8, 16])
+@pytest.mark.parametrize("r,form", [(8, 1), (8, 0), (16, 1), (16, 0), (18, 0), (32, 0)])
 def test_als_float64_retry_on_rank_deficient_rows(r, form):
     """Rows with fewer entries than the rank and a ridge of 1e-9 fail the float32
     pivot check; the float64 pass solves them and the result matches the oracle
-    (both forms of the half-step: tensor cores and lane-group SIMT)."""
+    (r <= 16: both forms of the half-step, tensor cores and lane-group SIMT; r = 18
+    and 32: the warp-per-line kernel, with factor rows of stride 18 read by scalar
+    loads and of stride 32 by 16-byte loads)."""
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_2202_12567_gb300 import lt
