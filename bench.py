@@ -53,7 +53,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-iso", action="store_true", help="skip the equal-error study of the two pass-2 pdfs")
     ap.add_argument("--frames-only", type=int, default=0,
-                    help="for profilers: set up, render this many plain frames and one graph replay, print no line")
+                    help="for profilers: set up, render this many plain frames and as many graph replays, print no line")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="with --frames-only: the pass-2 rate (the headline's, as the equal-error study chose it)")
+    ap.add_argument("--form", default="learned", choices=["learned", "g"],
+                    help="with --frames-only: the pass-2 pdf of the graph replays")
     return ap.parse_args()
 
 
@@ -238,12 +242,13 @@ OPS_ENTRY, OPS_RAY, OPS_CELL, OPS_BOX = 40, 40, 6, 24
 SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from one ncu
-# capture of each kernel on room256_vpl16k_2box; the summaries under profiles/ give
-# the commands.  A kernel changed since its capture has no entry here.
+# capture of each kernel on room256_vpl16k_2box at the headline's pass-2 rate (18%,
+# learned pdf), the median over the captured launches; profiles/traffic_room256_vpl16k_2box.md
+# gives the command.  A kernel changed since its capture has no entry here.
 MEASURED_TRAFFIC = {
-    "k_render": 7_060_480,
-    "k_eval_entries": 26_383_616 + 2_435_840,
-    "k_als_line": (41_023_744 + 42_821_120) // 2,  # U-step and V-step of one sweep, their mean
+    "k_render": 7_067_392,
+    "k_eval_entries": 32_962_688 + 3_178_240,
+    "k_als_line": 49_546_240,  # U-steps and V-steps of the captured frames
 }
 
 
@@ -543,6 +548,10 @@ def run_ours(args):
     # the held-out scenes' mean rel-RMSE and this scene's own are <= 2% (equal error),
     # the faster of the two; without a study, the preset's rate and the learned form.
     iso, headline = None, ("learned" if theta is not None else "g")
+    if args.frames_only:
+        headline = args.form if theta is not None else "g"
+        if args.rate > 0:
+            cfg["rate"] = args.rate
     if theta is not None and not args.frames_only and not args.no_iso:
         iso = proposal.iso_error(ctx, cfg, theta, [cfg["scene_seed"] + k for k in range(ISO_SCENES)], ISO_RATES,
                                  timing_scene=cfg["scene_seed"])
@@ -592,8 +601,13 @@ def run_ours(args):
     if args.frames_only:
         for i in range(args.frames_only):
             frame(100 + i)
-        g_only = lt.lt_frame_graph_capture(ctx, R.frame, lt.params(cfg), R.smp, R.uv, R.row_perm, R.img)
-        lt.lt_frame_graph_launch(g_only, seed0 + 200)
+        if headline == "learned":
+            g_only = lt.lt_frame_graph_capture(ctx, R.frame, lt.params(cfg, proposal=theta, mix=0.8), R.smp, R.uv,
+                                               R.row_perm, R.img, keep=(theta,))
+        else:
+            g_only = lt.lt_frame_graph_capture(ctx, R.frame, lt.params(cfg), R.smp, R.uv, R.row_perm, R.img)
+        for i in range(args.frames_only):
+            lt.lt_frame_graph_launch(g_only, seed0 + 200 + i)
         lt.lt_sync(ctx)
         torch.cuda.synchronize()
         return
