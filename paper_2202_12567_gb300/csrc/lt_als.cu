@@ -390,10 +390,13 @@ __global__ void k_als_init(lt_frame F, lt_samples smp, Omega om, int R, const in
 // ---- Gram of one line by one warp (ranks above 16) ---------------------------
 // For one line (a row of U or of V) with observed entries e and factor rows x_e,
 // G = sum_e x_e x_e^T and b = sum_e a_e x_e.  Lane k accumulates row k of G (all RP
-// columns; G is symmetric) and b_k: for each entry the warp reads x_e with 16-byte
-// loads at one warp-uniform address (a broadcast from L1/L2) and lane k its own
-// component x_e[k], then adds x_e[k] x_e and a_e x_e[k].  The rows have stride R;
-// components at or beyond R are zero.  Rows k of G go to Gs[RP][RP+1], b to bs[RP].
+// columns; G is symmetric) and b_k.  The entries are taken 32 at a time: lane l loads
+// the factor row of entry l with 16-byte loads and stages it in shared memory (the
+// line's Gram buffer, 16-byte chunk c of row l at chunk c ^ (l & 7) so that the
+// stores of eight lanes fill all banks), then for each staged row every lane reads
+// the whole row (broadcast loads) and its own component, and adds x_e[k] x_e and
+// a_e x_e[k].  The rows have stride R; components at or beyond R are zero.  At the
+// end rows k of G go to Gs[RP][RP+1] (over the stage) and b to bs[RP].
 template <int RP>  // RP == 32: lane k holds row k
 __device__ __forceinline__ void gram_warp(int len, const uint16_t* __restrict__ idx, const float* __restrict__ val,
                                           const float* __restrict__ src, int R, float* Gs, float* bs) {
@@ -401,40 +404,56 @@ __device__ __forceinline__ void gram_warp(int len, const uint16_t* __restrict__ 
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool vec = (R & 3) == 0 && ((uintptr_t)src & 15) == 0;
+    float4* xs4 = reinterpret_cast<float4*>(Gs);  // 32 staged rows of 8 chunks (4 KB <= the Gram buffer)
+    const float* xsf = Gs;
     float g[RP];
 #pragma unroll
     for (int c = 0; c < RP; ++c) g[c] = 0.f;
     float b = 0.f;
     for (int e0 = 0; e0 < len; e0 += 32) {
         const int n = min(32, len - e0);
-        const int je = lane < n ? (int)idx[e0 + lane] : 0;
-        const float ae = lane < n ? val[e0 + lane] : 0.f;
-#pragma unroll 2
-        for (int q = 0; q < n; ++q) {  // n is warp-uniform
-            const int j = __shfl_sync(FULL, je, q);
-            const float a = __shfl_sync(FULL, ae, q);
-            const float* xr = src + (int64_t)j * R;
-            float x[RP];
-            if (vec) {
+        const bool mine = lane < n;
+        const int j = mine ? (int)idx[e0 + lane] : 0;
+        const float av = mine ? val[e0 + lane] : 0.f;
+        const float* xr = src + (int64_t)j * R;
+        float4 t[RP / 4];
 #pragma unroll
-                for (int c4 = 0; c4 < RP / 4; ++c4) {
-                    const float4 t = 4 * c4 < R ? __ldg(reinterpret_cast<const float4*>(xr) + c4)
-                                                : make_float4(0.f, 0.f, 0.f, 0.f);
-                    x[4 * c4] = t.x;
-                    x[4 * c4 + 1] = t.y;
-                    x[4 * c4 + 2] = t.z;
-                    x[4 * c4 + 3] = t.w;
+        for (int c = 0; c < RP / 4; ++c) {
+            t[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mine) {
+                if (vec) {
+                    if (4 * c < R) t[c] = __ldg(reinterpret_cast<const float4*>(xr) + c);
+                } else {
+                    t[c].x = 4 * c < R ? __ldg(xr + 4 * c) : 0.f;
+                    t[c].y = 4 * c + 1 < R ? __ldg(xr + 4 * c + 1) : 0.f;
+                    t[c].z = 4 * c + 2 < R ? __ldg(xr + 4 * c + 2) : 0.f;
+                    t[c].w = 4 * c + 3 < R ? __ldg(xr + 4 * c + 3) : 0.f;
                 }
-            } else {
-#pragma unroll
-                for (int c = 0; c < RP; ++c) x[c] = c < R ? __ldg(xr + c) : 0.f;
             }
-            const float xk = lane < R ? __ldg(xr + lane) : 0.f;
+        }
+        __syncwarp();  // the previous chunk's rows have been read
+#pragma unroll
+        for (int c = 0; c < RP / 4; ++c) xs4[lane * 8 + (c ^ (lane & 7))] = t[c];
+        __syncwarp();
+        const int kc = lane >> 2, kw = lane & 3;
+        for (int q = 0; q < n; ++q) {  // n is warp-uniform
+            const float a = __shfl_sync(FULL, av, q);
+            float x[RP];
+#pragma unroll
+            for (int c = 0; c < RP / 4; ++c) {
+                const float4 u = xs4[q * 8 + (c ^ (q & 7))];
+                x[4 * c] = u.x;
+                x[4 * c + 1] = u.y;
+                x[4 * c + 2] = u.z;
+                x[4 * c + 3] = u.w;
+            }
+            const float xk = xsf[(q * 8 + (kc ^ (q & 7))) * 4 + kw];
             b = fmaf(a, xk, b);
 #pragma unroll
             for (int c = 0; c < RP; ++c) g[c] = fmaf(xk, x[c], g[c]);
         }
     }
+    __syncwarp();  // every lane is done with the staged rows
 #pragma unroll
     for (int c = 0; c < RP; ++c) Gs[lane * (RP + 1) + c] = g[c];
     bs[lane] = b;
@@ -443,6 +462,49 @@ __device__ __forceinline__ void gram_warp(int len, const uint16_t* __restrict__ 
 // A group of G lanes solves (Gram + ridge) u = b for one line: lane k holds row k of
 // the Gram in acc and b_k in rhs.  Returns false when the float factorisation is not
 // acceptable (a non-positive pivot, or pivots spread by more than 1/kPivotRatio).
+// Column J of the in-warp Cholesky and the columns after it, unrolled at compile
+// time (a loop whose inner bound depends on the outer index is not fully unrolled
+// by the compiler, and acc then lives in local memory)
+template <int G, typename T, int J>
+__device__ __forceinline__ void chol_col(T (&acc)[G], int k, int r, bool& ok, T& dmin, T& dmax) {
+    if constexpr (J < G) {
+        const unsigned FULL = 0xffffffffu;
+        const T djj = __shfl_sync(FULL, acc[J], J, G);
+        if (J < r) {
+            ok &= (djj > T(0));
+            dmin = djj < dmin ? djj : dmin;
+            dmax = djj > dmax ? djj : dmax;
+        }
+        const T dpos = djj > T(0) ? djj : T(1);
+        const T ljj = sqrt(dpos);
+        const T inv = T(1) / ljj;
+        const T lij = (k > J) ? acc[J] * inv : (k == J ? ljj : T(0));
+        acc[J] = lij;
+#pragma unroll
+        for (int c = J + 1; c < G; ++c) {
+            const T lcj = __shfl_sync(FULL, lij, c, G);
+            if (k > J) acc[c] -= lij * lcj;
+        }
+        chol_col<G, T, J + 1>(acc, k, r, ok, dmin, dmax);
+    }
+}
+
+// Step J of the backward substitution L^T x = y and the steps before it
+template <int G, typename T, int J>
+__device__ __forceinline__ void back_col(const T (&acc)[G], int k, T& x) {
+    if constexpr (J >= 0) {
+        const unsigned FULL = 0xffffffffu;
+        const T xj = __shfl_sync(FULL, x, J, G) / __shfl_sync(FULL, acc[J], J, G);
+        if (k == J) x = xj;
+#pragma unroll
+        for (int c = 0; c < J; ++c) {
+            const T ljc = __shfl_sync(FULL, acc[c], J, G);
+            if (k == c) x -= ljc * xj;
+        }
+        back_col<G, T, J - 1>(acc, k, x);
+    }
+}
+
 template <int G, typename T, bool SMEM_L>
 __device__ __forceinline__ bool factor_solve_rows(T (&acc)[G], T rhs, bool live, int len, int r, float lam_rel,
                                                   int k, T* out_k, bool check, float* Lsh) {
@@ -468,25 +530,7 @@ __device__ __forceinline__ bool factor_solve_rows(T (&acc)[G], T rhs, bool live,
     // right-looking Cholesky: lane i keeps row i; column j of L overwrites acc[j]
     T dmin = T(3.0e38), dmax = T(0);
     bool ok = true;
-#pragma unroll
-    for (int j = 0; j < G; ++j) {
-        T djj = __shfl_sync(FULL, acc[j], j, G);
-        if (j < r) {
-            ok &= (djj > T(0));
-            dmin = djj < dmin ? djj : dmin;
-            dmax = djj > dmax ? djj : dmax;
-        }
-        const T dpos = djj > T(0) ? djj : T(1);
-        const T ljj = sqrt(dpos);
-        const T inv = T(1) / ljj;
-        const T lij = (k > j) ? acc[j] * inv : (k == j ? ljj : T(0));
-        acc[j] = lij;
-#pragma unroll
-        for (int c = j + 1; c < G; ++c) {
-            const T lcj = __shfl_sync(FULL, lij, c, G);
-            if (k > j) acc[c] -= lij * lcj;
-        }
-    }
+    chol_col<G, T, 0>(acc, k, r, ok, dmin, dmax);
     if (check && !zero && (!ok || dmin < (T)kPivotRatio * dmax)) return false;
     if (SMEM_L) {
         // triangular solves through shared memory (Lsh may alias this line's Gram:
@@ -529,16 +573,7 @@ __device__ __forceinline__ bool factor_solve_rows(T (&acc)[G], T rhs, bool live,
     }
     // backward L^T x = y: x_j is final at step j; L[j][c] (c < j) comes from lane j
     T x = y;
-#pragma unroll
-    for (int j = G - 1; j >= 0; --j) {
-        const T xj = __shfl_sync(FULL, x, j, G) / __shfl_sync(FULL, acc[j], j, G);
-        if (k == j) x = xj;
-#pragma unroll
-        for (int c = 0; c < j; ++c) {
-            const T ljc = __shfl_sync(FULL, acc[c], j, G);
-            if (k == c) x -= ljc * xj;
-        }
-    }
+    back_col<G, T, G - 1>(acc, k, x);
     *out_k = (zero || k >= r) ? T(0) : x;
     return true;
 }
@@ -570,7 +605,7 @@ __global__ void __launch_bounds__(32 * als_warps<RP>(), 2) k_als_half(lt_frame F
                                                                    float* __restrict__ Fout, AlsQueue<RP> aq) {
     constexpr int LPW = 32 / RP;  // lines per warp
     constexpr int NW = als_warps<RP>();
-    __shared__ float Gs_all[NW][LPW][RP * (RP + 1)];
+    __shared__ __align__(16) float Gs_all[NW][LPW][RP * (RP + 1)];
     __shared__ float bs_all[NW][LPW][RP];
     const int s = blockIdx.y, P = gridDim.x, p = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
