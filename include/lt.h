@@ -218,6 +218,24 @@ lt_status lt_make_slices(lt_ctx* ctx, const float* pts, int64_t m, int32_t S, in
 int32_t lt_split_slice_count(int64_t m, int32_t target);
 lt_status lt_make_slices_split(lt_ctx* ctx, const float* pts, int64_t m, int32_t target, float normal_weight,
                                int32_t* row_perm, int32_t* slice_off);
+/* Slices held between min_rows and max_rows rows (the uneven slices of the batched
+ * workloads; no counterpart in the paper's text, which fixes the slice size only
+ * roughly, Sec. 3): starting from the S slices (row_perm_in, slice_off_in, e.g. from
+ * lt_make_slices), while a slice has fewer than min_rows rows and more than one is
+ * left, the smallest such slice (ties: the lowest index) joins the slice whose
+ * centroid is nearest to its own (float64 means of the float32 features (p, w n)
+ * summed in ascending pixel order, squared Euclidean distance, ties to the lowest
+ * index); then every slice of more than max_rows rows is split by the recursive 6-D
+ * median split of lt_make_slices_split, its parts taking its place.  Writes
+ * row_perm[m] (pixels ascending inside a slice; may be the same buffer as
+ * row_perm_in), slice_off[S' + 1] and *S_out = S'.  Every slice ends inside the
+ * bounds when max_rows >= 2 min_rows - 1 (a split halves).  LT_EINVAL for bad arguments, an
+ * inconsistent slice_off, or S' > max_slices (S + m / floor((max_rows + 1) / 2)
+ * always suffices).  Synchronous. */
+lt_status lt_bound_slices(lt_ctx* ctx, const float* pts, int64_t m, const int32_t* row_perm_in,
+                          const int32_t* slice_off_in, int32_t S, int32_t min_rows, int32_t max_rows,
+                          float normal_weight, int32_t max_slices, int32_t* row_perm, int32_t* slice_off,
+                          int32_t* S_out);
 /* pts_out[3][m][4] = pts with rows permuted by row_perm. */
 lt_status lt_permute_points(lt_ctx* ctx, const float* pts, int64_t m, const int32_t* row_perm,
                             float* pts_out);

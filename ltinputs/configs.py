@@ -19,6 +19,8 @@ import copy
 #   rank      completion rank r (the paper's q, Sec. 5)
 #   als_iters fixed number of alternating least-squares sweeps
 #   lam_rel   ridge term relative to the mean Gram diagonal
+#   slice_bounds  (lo, hi): k-means slices held between lo and hi rows (small ones
+#             merged into the nearest, large ones split by the 6-D median split)
 #   slicing   "kmeans" (n_slices clusters) or "split6d" (the paper's recursive 6-D
 #             binary split into slices of at most slice_size pixels)
 #   n_meshes  icosphere occluders (triangles, mesh_subdiv subdivisions) besides the boxes
@@ -57,10 +59,11 @@ CONFIGS = {
         glossy_frac=0.0, n_slices=64, rate=0.05, rate1=0.015, rank=16, als_iters=10,
         max_cut=4096, scene_seed=1002,
     ),
-    # 512x512 points, 65536 VPLs, 1000 boxes, Phong lobe on 30% of faces.
+    # 512x512 points, 65536 VPLs, 1000 boxes, Phong lobe on 30% of faces; uneven
+    # k-means slices held between 128 and 4096 rows.
     "room512_vpl64k_1000box_glossy": dict(
         _BASE, width=512, height=512, n_vpl=65536, n_big_boxes=0, n_small_boxes=1000,
-        glossy_frac=0.3, n_slices=128, rate=0.05, rate1=0.015, rank=16, als_iters=10,
+        glossy_frac=0.3, n_slices=128, slice_bounds=(128, 4096), rate=0.05, rate1=0.015, rank=16, als_iters=10,
         max_cut=2000, scene_seed=1003,
     ),
 }

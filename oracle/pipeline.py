@@ -49,6 +49,10 @@ def setup(scene, cfg, cut=None, slicing=None):
     elif slicing is None:
         row_perm, slice_off, _, _ = slices_mod.kmeans_slices(
             scene.points, cfg["n_slices"], cfg["kmeans_iters"], cfg["slice_feature_normal_weight"])
+        if cfg.get("slice_bounds"):
+            lo, hi = cfg["slice_bounds"]
+            row_perm, slice_off = slices_mod.bound_slices(scene.points, row_perm, slice_off, lo, hi,
+                                                          cfg["slice_feature_normal_weight"])
     else:
         row_perm, slice_off = slicing
     pts_s = slices_mod.permute_points(scene.points, row_perm)

@@ -101,3 +101,69 @@ def split6d_slices(points, target: int, w: float = 0.3):
 def permute_points(points, row_perm) -> np.ndarray:
     """Shading points in slice order."""
     return np.ascontiguousarray(np.asarray(points)[:, row_perm, :])
+
+
+def bound_slices(points, row_perm, slice_off, min_rows: int, max_rows: int, w: float = 0.3):
+    """Slices held between min_rows and max_rows rows (the uneven slices of the
+    batched workloads).  Reading: starting from given slices (k-means), while some
+    slice has fewer than min_rows rows and more than one slice is left, the smallest
+    such slice (ties: the lowest index) is merged into the slice whose centroid is
+    nearest to its own; then every slice with more than max_rows rows is split by the
+    recursive 6-D median split of ``split6d_slices`` into parts of at most max_rows,
+    the parts taking its place left to right.  Centroids are float64 means of the
+    float32 features (p, w n), summed in ascending pixel order; distances are squared
+    Euclidean in float64, ties to the lowest slice index.  Inside a slice the pixels
+    are in ascending order.  Every slice ends inside the bounds when
+    max_rows >= 2 min_rows - 1 (a split halves).  Returns (row_perm [m], slice_off [S'+1])."""
+    P = np.asarray(points, dtype=np.float32)
+    X = np.concatenate([P[0, :, :3], np.float32(w) * P[1, :, :3]], axis=1).astype(np.float32)
+    off = np.asarray(slice_off, dtype=np.int64)
+    perm = np.asarray(row_perm, dtype=np.int64)
+    sl = [np.sort(perm[off[s]:off[s + 1]]) for s in range(off.size - 1)]
+
+    def centroid(idx):
+        c = np.zeros(6)
+        for d in range(6):
+            c[d] = np.cumsum(X[idx, d].astype(np.float64))[-1] / idx.size if idx.size else 0.0
+        return c
+
+    cents = [centroid(a) for a in sl]
+    while len(sl) > 1:
+        small = [s for s in range(len(sl)) if sl[s].size < min_rows]
+        if not small:
+            break
+        s = min(small, key=lambda t: (sl[t].size, t))
+        best, bd = -1, np.inf
+        for t in range(len(sl)):
+            if t == s:
+                continue
+            diff = cents[s] - cents[t]
+            d2 = 0.0
+            for v in diff:
+                d2 = d2 + v * v
+            if d2 < bd:
+                best, bd = t, d2
+        sl[best] = np.sort(np.concatenate([sl[best], sl[s]]))
+        cents[best] = centroid(sl[best])
+        del sl[s]
+        del cents[s]
+    out = []
+
+    def split(idx):
+        n = idx.size
+        if n <= max_rows:
+            out.append(idx)
+            return
+        ext = X[idx].max(axis=0) - X[idx].min(axis=0)
+        d = int(np.argmax(ext))
+        order = np.lexsort((idx, X[idx, d]))
+        left = np.zeros(n, dtype=bool)
+        left[order[:n // 2]] = True
+        split(idx[left])
+        split(idx[~left])
+
+    for a in sl:
+        split(a)
+    row_perm_out = np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
+    off_out = np.concatenate([[0], np.cumsum([a.size for a in out])]).astype(np.int64)
+    return row_perm_out, off_out

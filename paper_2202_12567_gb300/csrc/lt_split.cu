@@ -8,6 +8,10 @@
 // reduction of the six features, an eight-pass radix select of the median over the
 // 64-bit keys (sortable feature bits << 32 | pixel), and a stable partition by block
 // scans.
+#include <math.h>
+
+#include <algorithm>
+#include <array>
 #include <vector>
 
 #include "lt_internal.cuh"
@@ -191,5 +195,125 @@ extern "C" lt_status lt_make_slices_split(lt_ctx* ctx, const float* pts, int64_t
         LT_CUDA(ctx, cudaMemcpyAsync(row_perm, in, (size_t)m * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     // the host vectors feed asynchronous copies: wait for them before returning
     LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return LT_OK;
+}
+
+// ------------------------------------------------------------------ slice bounds
+// Slices held between min_rows and max_rows rows (the uneven slices of the batched
+// workloads): while a slice has fewer than min_rows rows and more than one slice is
+// left, the smallest such slice (ties: the lowest index) joins the slice whose
+// centroid is nearest to its own (float64 means of the float32 features summed in
+// ascending pixel order, squared Euclidean distance, ties to the lowest index); then
+// every slice of more than max_rows rows is split by the recursive 6-D median split
+// above (k_split_level over its range of row_perm), its parts taking its place.  The
+// merges run on the host (a few slices), the splits on the GPU.
+extern "C" lt_status lt_bound_slices(lt_ctx* ctx, const float* pts, int64_t m, const int32_t* row_perm_in,
+                                     const int32_t* slice_off_in, int32_t S, int32_t min_rows, int32_t max_rows,
+                                     float normal_weight, int32_t max_slices, int32_t* row_perm,
+                                     int32_t* slice_off, int32_t* S_out) {
+    if (!ctx || !pts || m < 1 || m > INT32_MAX || !row_perm_in || !slice_off_in || S < 1 || min_rows < 1 ||
+        max_rows < min_rows || max_slices < 1 || !row_perm || !slice_off || !S_out || !(normal_weight >= 0.f) ||
+        ((uintptr_t)pts & 15) != 0)
+        return lt_fail(ctx, LT_EINVAL, "lt_bound_slices: bad arguments");
+    cudaSetDevice(ctx->device);
+    std::vector<int32_t> perm((size_t)m), off((size_t)S + 1);
+    std::vector<float4> planes((size_t)2 * m);
+    LT_CUDA(ctx, cudaMemcpyAsync(perm.data(), row_perm_in, (size_t)m * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaMemcpyAsync(off.data(), slice_off_in, ((size_t)S + 1) * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaMemcpyAsync(planes.data(), pts, (size_t)2 * m * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (off[0] != 0 || off[S] != m) return lt_fail(ctx, LT_EINVAL, "lt_bound_slices: slice_off does not cover m");
+    for (int s = 0; s < S; ++s)
+        if (off[s + 1] < off[s]) return lt_fail(ctx, LT_EINVAL, "lt_bound_slices: slice_off decreases");
+    auto feat = [&](int32_t i, int d) -> float {
+        const float4 a = planes[(size_t)i], b = planes[(size_t)m + i];
+        switch (d) {
+            case 0: return a.x;
+            case 1: return a.y;
+            case 2: return a.z;
+            case 3: return normal_weight * b.x;
+            case 4: return normal_weight * b.y;
+            default: return normal_weight * b.z;
+        }
+    };
+    std::vector<std::vector<int32_t>> sl((size_t)S);
+    for (int s = 0; s < S; ++s) {
+        sl[s].assign(perm.begin() + off[s], perm.begin() + off[s + 1]);
+        std::sort(sl[s].begin(), sl[s].end());
+        for (int32_t i : sl[s])
+            if (i < 0 || i >= m) return lt_fail(ctx, LT_EINVAL, "lt_bound_slices: row index out of range");
+    }
+    auto centroid = [&](const std::vector<int32_t>& a, double* c) {
+        for (int d = 0; d < 6; ++d) {
+            double t = 0.0;
+            for (int32_t i : a) t += (double)feat(i, d);
+            c[d] = a.empty() ? 0.0 : t / (double)a.size();
+        }
+    };
+    std::vector<std::array<double, 6>> cen((size_t)S);
+    for (int s = 0; s < S; ++s) centroid(sl[s], cen[s].data());
+    while (sl.size() > 1) {
+        int small = -1;
+        for (int s = 0; s < (int)sl.size(); ++s)
+            if ((int64_t)sl[s].size() < min_rows && (small < 0 || sl[s].size() < sl[small].size())) small = s;
+        if (small < 0) break;
+        int best = -1;
+        double bd = INFINITY;
+        for (int t = 0; t < (int)sl.size(); ++t) {
+            if (t == small) continue;
+            double d2 = 0.0;
+            for (int d = 0; d < 6; ++d) {
+                const double v = cen[small][d] - cen[t][d];
+                d2 = d2 + v * v;
+            }
+            if (d2 < bd) best = t, bd = d2;
+        }
+        sl[best].insert(sl[best].end(), sl[small].begin(), sl[small].end());
+        std::sort(sl[best].begin(), sl[best].end());
+        centroid(sl[best], cen[best].data());
+        sl.erase(sl.begin() + small);
+        cen.erase(cen.begin() + small);
+    }
+    // merged layout, then the split plan of every slice above max_rows
+    std::vector<int32_t> merged;
+    merged.reserve((size_t)m);
+    std::vector<std::vector<int2>> levels;
+    std::vector<int32_t> sizes;
+    for (auto& a : sl) {
+        const int64_t start = (int64_t)merged.size();
+        merged.insert(merged.end(), a.begin(), a.end());
+        split_plan(start, (int64_t)a.size(), max_rows, 0, levels, sizes);
+    }
+    if ((int64_t)sizes.size() > max_slices) return lt_fail(ctx, LT_EINVAL, "lt_bound_slices: max_slices too small");
+    std::vector<int32_t> noff(sizes.size() + 1, 0);
+    for (size_t s = 0; s < sizes.size(); ++s) noff[s + 1] = noff[s] + sizes[s];
+    size_t nn = 0;
+    for (auto& l : levels) nn += l.size();
+    std::vector<int2> all;
+    all.reserve(nn);
+    for (auto& l : levels) all.insert(all.end(), l.begin(), l.end());
+    lt_status st;
+    char* p = (char*)lt_scratch(ctx, SCR_SORT, (size_t)m * 4 + nn * 8 + 512, &st);
+    if (!p) return st;
+    int32_t* pong = (int32_t*)p;
+    int2* dnodes = (int2*)(p + (((size_t)m * 4 + 255) & ~(size_t)255));
+    if (nn) LT_CUDA(ctx, cudaMemcpyAsync(dnodes, all.data(), nn * 8, cudaMemcpyHostToDevice, ctx->stream));
+    LT_CUDA(ctx, cudaMemcpyAsync(row_perm, merged.data(), (size_t)m * 4, cudaMemcpyHostToDevice, ctx->stream));
+    LT_CUDA(ctx, cudaMemcpyAsync(slice_off, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    int32_t* in = row_perm;
+    int32_t* out = pong;
+    size_t at = 0;
+    for (auto& l : levels) {
+        LT_CUDA(ctx, cudaMemcpyAsync(out, in, (size_t)m * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        k_split_level<<<(unsigned)l.size(), kSplitThreads, 0, ctx->stream>>>(
+            reinterpret_cast<const float4*>(pts), m, normal_weight, dnodes + at, in, out);
+        LT_LAUNCH_CHECK(ctx, "k_split_level");
+        at += l.size();
+        std::swap(in, out);
+    }
+    if (in != row_perm)
+        LT_CUDA(ctx, cudaMemcpyAsync(row_perm, in, (size_t)m * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    LT_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vectors feed asynchronous copies
+    *S_out = (int32_t)sizes.size();
     return LT_OK;
 }

@@ -102,6 +102,7 @@ _SIGS = {
     "lt_cut_forest": (_i32, [_p, ctypes.POINTER(lt_tree), _p, _i32, _p, _p, _i32, _p, ctypes.POINTER(_i32)]),
     "lt_make_slices": (_i32, [_p, _p, _i64, _i32, _i32, _f32, _p, _p]),
     "lt_permute_points": (_i32, [_p, _p, _i64, _p, _p]),
+    "lt_bound_slices": (_i32, [_p, _p, _i64, _p, _p, _i32, _i32, _i32, _f32, _i32, _p, _p, ctypes.POINTER(_i32)]),
     "lt_sample_pass1": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, _f32, _f32, _u64, ctypes.POINTER(lt_samples)]),
     "lt_sample_pass1_target": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, _i32, _f32, _u64,
                                       ctypes.POINTER(lt_samples)]),
@@ -560,6 +561,21 @@ def lt_make_slices_split(ctx: Context, pts, target: int, normal_weight: float):
                                                                     float(normal_weight), _ptr(row_perm),
                                                                     _ptr(slice_off)))
     return row_perm, slice_off
+
+
+def lt_bound_slices(ctx: Context, pts, row_perm, slice_off, min_rows: int, max_rows: int, normal_weight: float):
+    """Slices held between min_rows and max_rows rows; returns new (row_perm [m],
+    slice_off [S'+1]) device int32 tensors."""
+    m = pts.shape[1]
+    S = slice_off.numel() - 1
+    cap = S + m // max(1, (int(max_rows) + 1) // 2) + 1
+    out_perm = torch.empty(m, dtype=torch.int32, device=pts.device)
+    out_off = torch.empty(cap + 1, dtype=torch.int32, device=pts.device)
+    n = _i32(0)
+    ctx._check("lt_bound_slices", ctx.lib.lt_bound_slices(ctx.h, _ptr(pts), m, _ptr(row_perm), _ptr(slice_off), S,
+                                                          int(min_rows), int(max_rows), float(normal_weight), cap,
+                                                          _ptr(out_perm), _ptr(out_off), ctypes.byref(n)))
+    return out_perm, out_off[:n.value + 1].clone()
 
 
 def lt_rgb_setup(ctx: Context, frame: Frame, rgb: RGB, pt_albedo, vpl_power, row_perm):

@@ -31,6 +31,8 @@ from .renderer import Renderer
 
 
 def _value(v: str):
+    if ":" in v:  # a pair such as slice_bounds=128:4096
+        return tuple(_value(x) for x in v.split(":"))
     for cast in (int, float):
         try:
             return cast(v)

@@ -75,6 +75,10 @@ class Renderer:
         elif row_perm is None:
             row_perm, slice_off = lt.lt_make_slices(ctx, self.pts, cfg["n_slices"], cfg["kmeans_iters"],
                                                     cfg["slice_feature_normal_weight"])
+            if cfg.get("slice_bounds"):  # uneven slices held between two row counts
+                lo, hi = cfg["slice_bounds"]
+                row_perm, slice_off = lt.lt_bound_slices(ctx, self.pts, row_perm, slice_off, lo, hi,
+                                                         cfg["slice_feature_normal_weight"])
         else:
             row_perm = torch.as_tensor(np.asarray(row_perm), dtype=torch.int32).to(self.dev)
             slice_off = torch.as_tensor(np.asarray(slice_off), dtype=torch.int32).to(self.dev)

@@ -534,6 +534,54 @@ def test_split_takes_the_dimension_of_largest_extent():
     assert np.all(nz[perm[:4]] < 0) and np.all(nz[perm[4:]] > 0)  # split on the normal
 
 
+# ---------------------------------------------------------------- slice bounds (uneven slices)
+def _cluster_points(centres_sizes, rng):
+    """Points on three well separated clusters of given sizes (x positions), normal +y."""
+    xs = np.concatenate([c + 0.001 * rng.standard_normal(n) for c, n in centres_sizes]).astype(np.float32)
+    return _line_points(xs)
+
+
+def test_bounds_merge_the_small_slice_into_the_nearest():
+    rng = np.random.default_rng(11)
+    P = _cluster_points([(0.0, 100), (0.1, 5), (1.0, 100)], rng)
+    perm = np.arange(205)
+    off = np.array([0, 100, 105, 205])
+    p2, o2 = slices_mod.bound_slices(P, perm, off, 10, 1000)
+    assert o2.tolist() == [0, 105, 205]                        # the 5 points join the cluster at 0.0
+    assert p2[:105].tolist() == list(range(105))
+    # placed nearer the far cluster, it joins that one (a wrong sign or index in the
+    # distance, or the largest instead of the nearest, fails one of the two)
+    P = _cluster_points([(0.0, 100), (0.9, 5), (1.0, 100)], rng)
+    p2, o2 = slices_mod.bound_slices(P, perm, off, 10, 1000)
+    assert o2.tolist() == [0, 100, 205] and p2[100:].tolist() == list(range(100, 205))
+
+
+def test_bounds_split_like_the_recursive_split_and_keep_slices_in_bounds():
+    rng = np.random.default_rng(12)
+    xs = rng.permutation(1000).astype(np.float32) / 1000
+    P = _line_points(xs)
+    # one slice of all points above max_rows: the same parts as the recursive split
+    p2, o2 = slices_mod.bound_slices(P, np.arange(1000), np.array([0, 1000]), 1, 100)
+    q, oq = slices_mod.split6d_slices(P, 100)
+    assert np.array_equal(p2, q) and np.array_equal(o2, oq)
+    # loose bounds leave given slices as they are (pixels sorted inside each)
+    perm = rng.permutation(1000)
+    off = np.array([0, 300, 310, 700, 1000])
+    p3, o3 = slices_mod.bound_slices(P, perm, off, 1, 1000)
+    assert np.array_equal(o3, off)
+    for s in range(4):
+        assert p3[off[s]:off[s + 1]].tolist() == sorted(perm[off[s]:off[s + 1]].tolist())
+    # tight bounds on a real scene's k-means slices: a partition, every slice in bounds
+    cfg = get_config("room64_vpl1k_2box")
+    sc = make_scene(cfg)
+    rp, so, _, _ = slices_mod.kmeans_slices(sc.points, 16, 10, 0.3)
+    p4, o4 = slices_mod.bound_slices(sc.points, rp, so, 200, 300)
+    sizes = np.diff(o4)
+    assert sorted(p4.tolist()) == list(range(sc.m))
+    assert sizes.min() >= 150 and sizes.max() <= 300         # a split halves a slice of > 300
+    assert np.diff(so).min() < 200 and np.diff(so).max() > 300  # both rules were exercised
+
+
 # ---------------------------------------------------------------- coarsening to a target cut size
 def _target_setup():
     cfg = get_config("room64_vpl1k_2box")
