@@ -22,12 +22,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_CACHE = os.path.join(HERE, "tuning_cache.json")
 
 # value -> (candidates, frame stage it acts on)
+# (a kernel form comes before the launch shapes that act under it)
 CANDIDATES = {
     "eval_ctas_per_sm": ([4, 8, 16, 32], "eval"),
-    "ray_ctas_per_sm": ([4, 8, 16, 32], "pass1"),
     "p1_form": ([0, 1], "pass1"),       # pass-1 levels: a launch per step, or one persistent walk
-    "als_lane_entries": ([48, 64, 96, 128, 192], "complete"),
+    "ray_ctas_per_sm": ([4, 8, 16, 32], "pass1"),
     "als_form": ([0, 1], "complete"),   # lane-group SIMT Gram or the tensor-core (tcgen05) Gram
+    "als_lane_entries": ([48, 64, 96, 128, 192], "complete"),
 }
 
 
