@@ -384,6 +384,47 @@ def rgb_leg(args, device: int, flush) -> dict | None:
     return out
 
 
+def temporal_leg(R, bf, flush, frames: int = 6) -> dict:
+    """Temporal coherence across frames (plain calls on the headline renderer): a chain
+    of frames of the static scene with new seeds, each completion started from the
+    previous frame's factors (lt_complete_warm) with fewer sweeps, against frames started
+    cold with the workload's sweeps: completion ms and rel-RMSE of the chain's last frame
+    against the brute force."""
+    import torch
+
+    cfg = R.cfg
+    nbf = torch.linalg.norm(bf.double())
+    out = {}
+    for name, warm, iters in (("cold", False, cfg["als_iters"]), ("warm_5", True, 5), ("warm_3", True, 3),
+                              ("warm_2", True, 2), ("warm_1", True, 1)):
+        R._prev = None
+        if warm:
+            R.render(seed=cfg["frame_seed"] + 300, warm=True)  # the chain's first frame, started cold
+        tc, tf = [], []
+        for k in range(frames):
+            flush.zero_()
+            seed = cfg["frame_seed"] + 301 + k
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record()
+            R.pass1(seed)
+            R.pass2(seed)
+            R.evaluate()
+            ev[1].record()
+            R.complete(seed, warm=warm, iters=iters)
+            R.render_image()
+            ev[2].record()
+            torch.cuda.synchronize()
+            tc.append(ev[1].elapsed_time(ev[2]))
+            tf.append(ev[0].elapsed_time(ev[2]))
+        rel = float(torch.linalg.norm(R.img.double() - bf.double()) / nbf)
+        out[name] = dict(sweeps=iters, completion_ms=round(statistics.median(tc), 3),
+                         frame_ms=round(statistics.median(tf), 3), rel_rmse=round(rel, 5))
+    R._prev = None
+    out["chain"] = (f"{frames} frames of the same scene with new seeds, plain calls, pass-2 pdf g at the "
+                    f"headline's rate; warm: each completion started from the previous frame's factors")
+    return out
+
+
 def mesh_leg(args, device: int, flush) -> dict | None:
     """The workload with triangle-mesh occluders (icospheres through a BVH) besides the
     boxes, plain calls on a context of its own: ms/frame and rel-RMSE against the GPU
@@ -772,6 +813,10 @@ def run_ours(args):
         meshes = mesh_leg(args, local, flush)
     except RuntimeError as e:
         meshes = dict(error=str(e))
+    try:
+        temporal = temporal_leg(R, bf, flush)
+    except RuntimeError as e:
+        temporal = dict(error=str(e))
 
     line = dict(metric=METRIC, value=round(ms_frame, 4), unit="ms/frame", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=round(total_ms / args.steps, 4), higher_is_better=False,
@@ -803,6 +848,7 @@ def run_ours(args):
                             adm_completion=adm,
                             rgb=colour,
                             mesh=meshes,
+                            temporal=temporal,
                             setup_ms=round(setup_ms, 1),
                             setup_breakdown_ms=R.setup_ms,
                             setup_plus_one_plain_frame_ms=round(setup_ms + plain_ms, 2),

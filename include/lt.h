@@ -296,6 +296,18 @@ lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, const lt_sa
  * line's Gram again in float64 and solves it in float64). */
 lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
                       float lam_rel, uint64_t seed, lt_factors* uv);
+/* Temporal coherence across frames (Sec. 7 leaves it to future work; this form is
+ * ours): lt_complete started from a previous frame's factors.  Column c of slice s
+ * whose coarsened-cut node (smp->col_node, a tree node id) was column i of the
+ * previous frame's slice s (prev_col_node [S][C], prev_ncol [S]) starts from the
+ * previous V row i (prev_V [S][C][uv->r]; its components below the slice's rank,
+ * zero beyond), every other column from the seeded start of lt_complete; then
+ * `iters` sweeps as lt_complete.  The previous arrays are device memory that the
+ * caller keeps (prev_V must not be uv->V).  LT_EINVAL as lt_complete, or for null
+ * previous arrays. */
+lt_status lt_complete_warm(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
+                           float lam_rel, uint64_t seed, const int32_t* prev_col_node, const int32_t* prev_ncol,
+                           const float* prev_V, lt_factors* uv);
 /* The tensor-core contraction of one ALS half-step alone, a check of the Gram
  * matrices of the completion (Sec. 5; lt_complete with als_form 1).  Side 0: every
  * row i of every slice gets G_i = sum_j v_j v_j^T and b_i = sum_j A_ij v_j over its

@@ -13,6 +13,8 @@ the sampled entries.  The completion used here is masked alternating least squar
   a row without entries, or with trace(G_i) = 0, gets u_i = 0.  The V-step is the
   same per column with the roles of U and V swapped.
 * A fixed number of iterations is run (the paper stops on a tolerance or after 100).
+* Across frames (warm_start): a column whose node was a column of the previous
+  frame's slice starts from its previous V row.
 """
 from __future__ import annotations
 
@@ -26,6 +28,28 @@ def init_v(seed: int, s: int, n_s: int, r: int, mu: float) -> np.ndarray:
     j = np.arange(n_s, dtype=np.uint64)[:, None]
     w = philox.draw(seed, k, j, s, philox.TAG_ALSINIT)[0].astype(np.float64)
     return np.sqrt(max(mu, 0.0) / r) * (0.5 + w / 2.0 ** 32)
+
+
+def warm_start(seed: int, s: int, col_node, vals, r: int, prev_col_node, prev_V) -> np.ndarray:
+    """Start of a frame's completion from the previous frame's factors (temporal
+    coherence, which the paper leaves to future work, Sec. 7; the form is ours): a
+    column whose coarsened-cut node (tree node id) was also a column of the same slice
+    in the previous frame starts from that column's V row (its first r components,
+    zero beyond the previous rank), every other column from init_v."""
+    vals = np.asarray(vals, dtype=np.float64)
+    mu = float(vals.mean()) if vals.size else 0.0
+    col_node = np.asarray(col_node)
+    V = init_v(seed, s, col_node.size, r, mu)
+    prev_V = np.asarray(prev_V, dtype=np.float64)
+    where = {int(n): i for i, n in enumerate(np.asarray(prev_col_node).tolist())}
+    for c, n in enumerate(col_node.tolist()):
+        i = where.get(int(n))
+        if i is not None:
+            row = np.zeros(r)
+            k = min(r, prev_V.shape[1])
+            row[:k] = prev_V[i, :k]
+            V[c] = row
+    return V
 
 
 def _half_step(idx_a, idx_b, vals, n_a, F, r, lam_rel):

@@ -60,7 +60,7 @@ def setup(scene, cfg, cut=None, slicing=None):
                 slice_off=np.asarray(slice_off), pts_s=pts_s)
 
 
-def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceResult:
+def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None, prev=None) -> SliceResult:
     tree, forest, pts_s = st["tree"], st["forest"], st["pts_s"]
     a, b = int(st["slice_off"][s]), int(st["slice_off"][s + 1])
     m_s = b - a
@@ -81,8 +81,12 @@ def run_slice(st, scene, cfg, s, seed, weights=None, order_rng=None) -> SliceRes
         res.U, res.V = adm.complete_slice_adm(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["adm_iters"],
                                               cfg["adm_alpha_rel"], cfg["adm_gamma"], seed, s)
     else:
-        res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, slice_rank(cfg, n_s), cfg["als_iters"],
-                                          cfg["lam_rel"], seed, s)
+        r = slice_rank(cfg, n_s)
+        V0 = None
+        if prev is not None:  # the previous frame's result of this slice: start from its factors
+            V0 = als.warm_start(seed, s, p1.col_node, vals, r, prev.p1.col_node, prev.V)
+        res.U, res.V = als.complete_slice(rows, cols, vals, m_s, n_s, r, cfg["als_iters"], cfg["lam_rel"], seed, s,
+                                          V0=V0)
     return res
 
 
@@ -103,15 +107,17 @@ def slice_rank(cfg, n_s: int) -> int:
     return int(min(cfg["rank"], max(8, 8 * -(-int(n_s) // cols))))
 
 
-def render_frame(scene, cfg, st=None, seed=None, slices=None):
-    """Run steps 3-5 for every slice (or the listed ones); returns (image, per-slice results)."""
+def render_frame(scene, cfg, st=None, seed=None, slices=None, prev=None):
+    """Run steps 3-5 for every slice (or the listed ones); returns (image, per-slice
+    results).  prev: the previous frame's per-slice results, whose factors start this
+    frame's completion (als.warm_start)."""
     st = setup(scene, cfg) if st is None else st
     seed = cfg["frame_seed"] if seed is None else seed
     S = len(st["slice_off"]) - 1
     todo = range(S) if slices is None else slices
     results = {}
     for s in todo:
-        results[s] = run_slice(st, scene, cfg, s, seed)
+        results[s] = run_slice(st, scene, cfg, s, seed, prev=None if prev is None else prev.get(s))
     factors = []
     for s in range(S):
         if s in results:

@@ -1198,8 +1198,45 @@ lt_status omega_build(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int
 
 }  // namespace ltk
 
-extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
-                                 float lam_rel, uint64_t seed, lt_factors* uv) {
+namespace {
+
+// The previous frame's columns and factors that start a frame's completion
+struct WarmStart {
+    const int32_t* col_node;   // [S][C] tree node of each previous column
+    const int32_t* ncol;       // [S]    previous columns per slice
+    const float* V;            // [S][C][R] previous V rows
+};
+
+// Temporal coherence: column c of slice s whose node was a column i of the previous
+// frame's slice s starts from the previous V row i (components below the slice's
+// rank; the previous rows are zero beyond their own rank), the others keep the
+// seeded start.  One CTA per slice; the previous node list is staged in shared memory
+// and searched linearly (the cut is not sorted by node id).
+__global__ void __launch_bounds__(256) k_als_warm(lt_frame F, lt_samples smp, int R, const int32_t* __restrict__ rk,
+                                                  WarmStart w, float* __restrict__ V) {
+    extern __shared__ int32_t pn[];
+    const int s = blockIdx.x;
+    const int np = min(w.ncol[s], F.C), ns = smp.ncol[s];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) pn[i] = w.col_node[(int64_t)s * F.C + i];
+    __syncthreads();
+    const int r = slice_rank(rk, s, R);
+    for (int c = threadIdx.x; c < ns; c += blockDim.x) {
+        const int node = smp.col_node[(int64_t)s * F.C + c];
+        int hit = -1;
+        for (int i = 0; i < np; ++i)
+            if (pn[i] == node) {
+                hit = i;
+                break;
+            }
+        if (hit < 0) continue;
+        const float* src = w.V + ((int64_t)s * F.C + hit) * R;
+        float* dst = V + ((int64_t)s * F.C + c) * R;
+        for (int k = 0; k < R; ++k) dst[k] = k < r ? src[k] : 0.f;
+    }
+}
+
+lt_status complete_impl(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters, float lam_rel,
+                        uint64_t seed, lt_factors* uv, const WarmStart* warm) {
     if (!ctx || !frame_ok2(f) || !smp || !smp->key || !smp->val || !smp->off || !smp->cnt || !smp->ncol || !uv ||
         !uv->U || !uv->V || uv->r < 1 || uv->r > 32 || iters < 0 || !(lam_rel >= 0.f))
         return lt_fail(ctx, LT_EINVAL, "lt_complete: bad arguments");
@@ -1239,6 +1276,13 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
     const int nsm = ctx->num_sms;
     k_als_init<<<dim3(8, S), 256, 0, ctx->stream>>>(*f, *smp, om, R, rk, seed_ref(ctx, seed), uv->V);
     LT_LAUNCH_CHECK(ctx, "k_als_init");
+    if (warm) {
+        const size_t shm = (size_t)C * 4;
+        if (shm > 48 * 1024)
+            LT_CUDA(ctx, cudaFuncSetAttribute(k_als_warm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+        k_als_warm<<<S, 256, shm, ctx->stream>>>(*f, *smp, R, rk, *warm, uv->V);
+        LT_LAUNCH_CHECK(ctx, "k_als_warm");
+    }
     // lane-group kernel: one thread (group) per line; one 256-thread CTA per SM stages
     // the slice's factor rows (up to 110 KB) and leaves the rest of the SM to L1
     const size_t row_bytes = (size_t)RP * 4;
@@ -1323,6 +1367,22 @@ extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_sample
         }
     }
     return LT_OK;
+}
+
+}  // namespace
+
+extern "C" lt_status lt_complete(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
+                                 float lam_rel, uint64_t seed, lt_factors* uv) {
+    return complete_impl(ctx, f, smp, iters, lam_rel, seed, uv, nullptr);
+}
+
+extern "C" lt_status lt_complete_warm(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, int32_t iters,
+                                      float lam_rel, uint64_t seed, const int32_t* prev_col_node,
+                                      const int32_t* prev_ncol, const float* prev_V, lt_factors* uv) {
+    if (!prev_col_node || !prev_ncol || !prev_V || (uv && prev_V == uv->V))
+        return lt_fail(ctx, LT_EINVAL, "lt_complete_warm: bad arguments");
+    const WarmStart w{prev_col_node, prev_ncol, prev_V};
+    return complete_impl(ctx, f, smp, iters, lam_rel, seed, uv, &w);
 }
 
 extern "C" lt_status lt_als_gram(lt_ctx* ctx, const lt_frame* f, const lt_samples* smp, const lt_factors* uv,

@@ -112,6 +112,8 @@ _SIGS = {
     "lt_eval_entries_noalloc": (_i32, [_p, ctypes.POINTER(lt_frame), _f32, ctypes.POINTER(lt_samples)]),
     "lt_complete": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _u64,
                            ctypes.POINTER(lt_factors)]),
+    "lt_complete_warm": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _u64, _p, _p,
+                                _p, ctypes.POINTER(lt_factors)]),
     "lt_complete_adm": (_i32, [_p, ctypes.POINTER(lt_frame), ctypes.POINTER(lt_samples), _i32, _f32, _f32, _u64,
                                ctypes.POINTER(lt_factors)]),
     "lt_mesh_upload": (_i32, [_p, _p, _i64]),
@@ -507,6 +509,16 @@ def lt_eval_stats(ctx: Context, frame: Frame, smp: Samples, d_min) -> dict:
 def lt_complete(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, lam_rel, seed):
     ctx._check("lt_complete", ctx.lib.lt_complete(ctx.h, ctypes.byref(frame.struct()), ctypes.byref(smp.struct()),
                                                   iters, lam_rel, seed, ctypes.byref(uv.struct())))
+
+
+def lt_complete_warm(ctx: Context, frame: Frame, smp: Samples, uv: Factors, iters, lam_rel, seed, prev_col_node,
+                     prev_ncol, prev_V):
+    """lt_complete started from a previous frame's columns and V (device tensors the
+    caller keeps; prev_V is not uv.V)."""
+    ctx._check("lt_complete_warm", ctx.lib.lt_complete_warm(ctx.h, ctypes.byref(frame.struct()),
+                                                            ctypes.byref(smp.struct()), iters, lam_rel, seed,
+                                                            _ptr(prev_col_node), _ptr(prev_ncol), _ptr(prev_V),
+                                                            ctypes.byref(uv.struct())))
 
 
 def lt_als_gram(ctx: Context, frame: Frame, smp: Samples, uv: Factors, side: int):

@@ -108,26 +108,36 @@ class Renderer:
     def evaluate(self):
         lt.lt_eval_entries(self.ctx, self.frame, self.smp, self.cfg["d_min"])
 
-    def complete(self, seed):
+    def complete(self, seed, warm=False, iters=None):
+        """warm: start from the previous warm frame's factors (lt_complete_warm) and keep
+        this frame's for the next; iters: sweeps instead of the workload's."""
         c = self.cfg
+        iters = c["als_iters"] if iters is None else int(iters)
         if int(c.get("rank_cols", 0)) > 0:  # per-slice ranks from the coarsened cut
             lt.lt_slice_ranks(self.ctx, self.frame, self.smp, c["rank"], c["rank_cols"], self.uv.rank)
         if c.get("completion", "als") == "adm":  # nonnegative completion (App. A)
             lt.lt_complete_adm(self.ctx, self.frame, self.smp, self.uv, c["adm_iters"], c["adm_alpha_rel"],
                                c["adm_gamma"], seed)
+            return
+        prev = getattr(self, "_prev", None)
+        if warm and prev is not None:  # temporal coherence: the previous frame's factors
+            lt.lt_complete_warm(self.ctx, self.frame, self.smp, self.uv, iters, c["lam_rel"], seed, *prev)
         else:
-            lt.lt_complete(self.ctx, self.frame, self.smp, self.uv, c["als_iters"], c["lam_rel"], seed)
+            lt.lt_complete(self.ctx, self.frame, self.smp, self.uv, iters, c["lam_rel"], seed)
+        if warm:
+            self._prev = (self.smp.col_node.clone(), self.smp.ncol.clone(), self.uv.V.clone())
 
     def render_image(self, w=None):
         lt.lt_render(self.ctx, self.frame, self.smp, self.uv, self.row_perm, self.img, w)
 
-    def render(self, seed=None, weights=None, sync=True):
-        """One frame: pass 1, pass 2, entry evaluation, completion, image."""
+    def render(self, seed=None, weights=None, sync=True, warm=False, iters=None):
+        """One frame: pass 1, pass 2, entry evaluation, completion, image (warm, iters:
+        see complete)."""
         seed = self.cfg["frame_seed"] if seed is None else seed
         self.pass1(seed)
         self.pass2(seed, weights)
         self.evaluate()
-        self.complete(seed)
+        self.complete(seed, warm=warm, iters=iters)
         self.render_image()
         if sync:
             lt.lt_sync(self.ctx)

@@ -423,6 +423,41 @@ def test_als_fully_observed_reaches_truncated_svd():
     assert abs(err - best) / best < 1e-6
 
 
+def test_warm_start_maps_columns_by_node():
+    """Columns whose node was a previous column start from its V row (first r
+    components, zero beyond the previous rank); the others from the seeded start."""
+    rng = np.random.default_rng(6)
+    prev_nodes = np.array([40, 7, 19, 3])
+    prev_V = rng.uniform(0.1, 1.0, (4, 5))
+    nodes = np.array([3, 11, 40, 19])             # 11 is new
+    vals = rng.uniform(0.0, 2.0, 50)
+    V0 = als.warm_start(9, 2, nodes, vals, 8, prev_nodes, prev_V)
+    cold = als.init_v(9, 2, 4, 8, float(vals.mean()))
+    for c, i in ((0, 3), (2, 0), (3, 2)):
+        assert np.array_equal(V0[c, :5], prev_V[i]) and np.all(V0[c, 5:] == 0.0)
+    assert np.array_equal(V0[1], cold[1])
+    # a lower rank keeps the first components
+    assert np.array_equal(als.warm_start(9, 2, nodes, vals, 3, prev_nodes, prev_V)[0], prev_V[3, :3])
+
+
+def test_warm_start_from_the_answer_needs_one_sweep():
+    """Started at the true V of an exactly rank-r matrix, one sweep recovers it; the
+    seeded start does not (a start that ignored the previous factors fails this)."""
+    rng = np.random.default_rng(8)
+    m, n, r = 80, 60, 4
+    X = rng.uniform(0.1, 1.0, (m, r))
+    Y = rng.uniform(0.1, 1.0, (n, r))
+    M = X @ Y.T
+    idx = rng.choice(m * n, 3 * r * (m + n), replace=False)
+    rows, cols = idx // n, idx % n
+    nodes = np.arange(100, 100 + n)
+    V0 = als.warm_start(1, 0, nodes, M[rows, cols], r, nodes, Y)
+    U, V = als.complete_slice(rows, cols, M[rows, cols], m, n, r, 1, 1e-12, 1, 0, V0=V0)
+    assert np.linalg.norm(U @ V.T - M) / np.linalg.norm(M) <= 1e-6
+    U, V = als.complete_slice(rows, cols, M[rows, cols], m, n, r, 1, 1e-12, 1, 0)
+    assert np.linalg.norm(U @ V.T - M) / np.linalg.norm(M) > 1e-3
+
+
 @pytest.mark.parametrize("n_s,R,cols,want", [
     # values worked out by hand from r_s = min(R, max(8, 8 * ceil(n' / cols)))
     (0, 32, 512, 8), (1, 32, 512, 8), (511, 32, 512, 8), (512, 32, 512, 8), (513, 32, 512, 16),
