@@ -3,8 +3,8 @@
 Every function here has the name of the C entry point it wraps and does no
 computation of its own: device memory comes from PyTorch tensors, whose raw
 pointers are handed to the library, and every step runs in the library's CUDA
-kernels.  Importing this module loads liblt.so and fails loudly when it is
-missing; there is no fallback path.
+kernels.  The first context (or an explicit load()) loads liblt.so and fails
+loudly when it is missing; there is no fallback path.
 """
 from __future__ import annotations
 
