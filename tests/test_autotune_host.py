@@ -25,3 +25,9 @@ def test_candidates_are_valid_tuning_values():
             assert cands == [0, 1]
         else:
             assert all(16 <= c <= 1024 for c in cands)
+
+
+def test_each_form_is_tuned_before_the_shapes_that_act_under_it():
+    names = list(autotune.CANDIDATES)
+    assert names.index("p1_form") < names.index("ray_ctas_per_sm")
+    assert names.index("als_form") < names.index("als_lane_entries")
