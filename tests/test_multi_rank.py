@@ -45,13 +45,13 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, out):
+def _rank_main(rank, world, port, out, extra=None):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from ltinputs import get_config, make_scene
         from oracle import pipeline
-        cfg = get_config("room64_vpl1k_2box", max_cut=64, n_slices=8)
+        cfg = get_config("room64_vpl1k_2box", max_cut=64, n_slices=8, **(extra or {}))
         sc = make_scene(cfg)
         st = pipeline.setup(sc, cfg)
         parts = shard.lpt_partition(shard.slice_costs(st["slice_off"], C=len(st["cut"])), world)
@@ -82,6 +82,24 @@ def test_two_ranks_render_the_single_process_frame(tmp_path):
     got = np.load(out)
     assert np.array_equal(got, want)
     assert float(open(out + ".t").read()) == 11.0
+
+
+@pytest.mark.slow
+def test_two_ranks_with_bounded_slices(tmp_path):
+    """The same with slices held between 450 and 900 rows (8 k-means slices become 6:
+    small ones merged, none above the bound), so the split runs over the bounded
+    slice count."""
+    from ltinputs import get_config, make_scene
+    from oracle import pipeline
+    extra = dict(slice_bounds=(450, 900))
+    out = str(tmp_path / "img.npy")
+    mp.start_processes(_rank_main, args=(2, _free_port(), out, extra), nprocs=2, join=True, start_method="spawn")
+    cfg = get_config("room64_vpl1k_2box", max_cut=64, n_slices=8, **extra)
+    sc = make_scene(cfg)
+    st = pipeline.setup(sc, cfg)
+    assert len(st["slice_off"]) - 1 == 6
+    want, _ = pipeline.render_frame(sc, cfg, st)
+    assert np.array_equal(np.load(out), want)
 
 
 def _rank_main_rgb(rank, world, port, out):
