@@ -247,7 +247,6 @@ SMS, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
 # gives the command.  A kernel changed since its capture has no entry here.
 MEASURED_TRAFFIC = {
     "k_render": 7_067_392,
-    "k_eval_entries": 32_962_688 + 3_178_240,
     "k_als_line": 49_546_240,  # U-steps and V-steps of the captured frames
 }
 

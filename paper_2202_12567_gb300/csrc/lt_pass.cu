@@ -12,7 +12,8 @@
 //    the integer CDF of g or of given weights, row uniform) in rounds, keeps the
 //    first occurrence of every new entry in draw order, and stops at
 //    ceil(rate m' n') entries.
-//  * Entry evaluation: one thread per pass-2 entry (one shadow ray).
+//  * Entry evaluation: one thread per pass-2 entry (one shadow ray), the column side
+//    read from per-frame column records (k_col_records).
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -1109,9 +1110,30 @@ __global__ void k_count_prefix(const lt_samples smp, int S, int64_t* pfx) {
     if (threadIdx.x == 0) pfx[S] = carry;
 }
 
+// Column records of a frame: for every (slice, coarsened column) the representative
+// VPL's three record planes and the node's scale I_c / (flux albedo) of its
+// representative, 64 B each ([S][C][4] float4), so that an entry gathers its column
+// with one contiguous load (a slice's few hundred columns stay in L1) instead of the
+// node, its representative, the three VPL planes and three scale terms.
+__global__ void k_col_records(lt_frame F, lt_samples smp, float4* __restrict__ tab) {
+    const int s = blockIdx.y;
+    const int ns = smp.ncol[s];
+    const float4* vpls = reinterpret_cast<const float4*>(F.vpls);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ns; c += gridDim.x * blockDim.x) {
+        const int node = smp.col_node[(int64_t)s * F.C + c];
+        const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
+        float4* t = tab + ((int64_t)s * F.C + c) * 4;
+        t[0] = L.a;
+        t[1] = L.b;
+        t[2] = L.c;
+        t[3] = make_float4(node_scale(F.tree, vpls, F.n, node), 0.f, 0.f, 0.f);
+    }
+}
+
 template <bool COUNT>
 __global__ void __launch_bounds__(128) k_eval_entries(lt_frame F, Grid g, float dmin2, lt_samples smp,
                                                       const int64_t* __restrict__ pfx,
+                                                      const float4* __restrict__ coltab,
                                                       unsigned long long* __restrict__ stats, int32_t* status) {
     extern __shared__ int64_t spfx[];
     const int S = F.S;
@@ -1134,10 +1156,21 @@ __global__ void __launch_bounds__(128) k_eval_entries(lt_frame F, Grid g, float 
         const int64_t e = smp.off[s] + smp.n1[s] + (idx - spfx[s]);
         const uint32_t k = smp.key[e];
         const int r = (int)(k >> 16), c = (int)(k & 0xffffu);
-        const int node = smp.col_node[(int64_t)s * F.C + c];
         const PointRec P = load_rec(pts, F.m, F.slice_off[s] + r);
-        const PointRec L = load_rec(vpls, F.n, F.tree.rep[node]);
-        const float v = entry_value<COUNT>(P, L, node_scale(F.tree, vpls, F.n, node), dmin2, g, &wc, &rays);
+        PointRec L;
+        float scale;
+        if (coltab) {  // the frame's column records
+            const float4* t = coltab + ((int64_t)s * F.C + c) * 4;
+            L.a = __ldg(t);
+            L.b = __ldg(t + 1);
+            L.c = __ldg(t + 2);
+            scale = __ldg(t + 3).x;
+        } else {
+            const int node = smp.col_node[(int64_t)s * F.C + c];
+            L = load_rec(vpls, F.n, F.tree.rep[node]);
+            scale = node_scale(F.tree, vpls, F.n, node);
+        }
+        const float v = entry_value<COUNT>(P, L, scale, dmin2, g, &wc, &rays);
         if (COUNT) {
             ++entries;
         } else {
@@ -1382,16 +1415,21 @@ extern "C" lt_status lt_eval_entries(lt_ctx* ctx, const lt_frame* f, float d_min
     if (!ctx->d_cell_off) return lt_fail(ctx, LT_EINVAL, "lt_eval_entries: no scene uploaded");
     cudaSetDevice(ctx->device);
     lt_status st;
-    int64_t* pfx = (int64_t*)lt_scratch(ctx, SCR_MISC, (size_t)(f->S + 1) * 8, &st);
-    if (!pfx) return st;
+    const size_t apfx = ((size_t)(f->S + 1) * 8 + 255) & ~(size_t)255;
+    char* p = (char*)lt_scratch(ctx, SCR_MISC, apfx + (size_t)f->S * f->C * 64, &st);
+    if (!p) return st;
+    int64_t* pfx = (int64_t*)p;
+    float4* tab = (float4*)(p + apfx);
     k_count_prefix<<<1, 1024, 0, ctx->stream>>>(*smp, f->S, pfx);
     LT_LAUNCH_CHECK(ctx, "k_count_prefix");
+    k_col_records<<<dim3((unsigned)std::min(16, (f->C + 255) / 256), f->S), 256, 0, ctx->stream>>>(*f, *smp, tab);
+    LT_LAUNCH_CHECK(ctx, "k_col_records");
     const size_t shm = (size_t)(f->S + 1) * 8;
     if (shm > 16 * 1024)
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
     k_eval_entries<false><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
-                                                                        nullptr, ctx->d_status);
+                                                                        tab, nullptr, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries");
     return LT_OK;
 }
@@ -1459,7 +1497,7 @@ extern "C" lt_status lt_eval_entries_noalloc(lt_ctx* ctx, const lt_frame* f, flo
         LT_CUDA(ctx, cudaFuncSetAttribute(k_eval_entries<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)shm));
     k_eval_entries<false><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, *smp, pfx,
-                                                                        nullptr, ctx->d_status);
+                                                                        nullptr, nullptr, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries");
     return LT_OK;
 }
@@ -1484,7 +1522,7 @@ extern "C" lt_status lt_eval_stats(lt_ctx* ctx, const lt_frame* f, float d_min, 
                                           (int)shm));
     lt_samples copy = *smp;
     k_eval_entries<true><<<ctx->num_sms * ctx->tune.eval_ctas_per_sm, 128, shm, ctx->stream>>>(*f, ctx->grid, d_min * d_min, copy, pfx,
-                                                                       stats, ctx->d_status);
+                                                                       nullptr, stats, ctx->d_status);
     LT_LAUNCH_CHECK(ctx, "k_eval_entries<count>");
     unsigned long long h[4];
     LT_CUDA(ctx, cudaMemcpyAsync(h, stats, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
